@@ -1,0 +1,318 @@
+"""Benchmark: FTLM H.v throughput in states x vectors per second.
+
+One step = one whole FTLM run (all rows of the hot path): start block of R
+random vectors, M Lanczos steps (matvec with fused reductions, recurrence
+update), tridiagonal eigensolves and the Boltzmann sums of Eqs. (4)-(5), on
+the open 4x5 s=1/2 lattice with all-pairs dipolar coupling (N = 20,
+d = 1,048,576, R = 64, M = 200, complex64 vectors with FP32 matvec and FP64
+scalars).  value = d * R * M * steps * n_gpus / time, time from CUDA events
+on the run's stream (max over ranks).
+
+--impl reference times the FP64 CPU oracle instead, on bounded samples of
+the same workload (R = number of oracle threads, a few Lanczos steps).
+
+Multi-GPU (torchrun): every rank runs its own R vectors (vec_offset =
+rank * R); no collective touches the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ftlm_workloads as W  # noqa: E402
+
+METRIC = "FTLM H·v states×vectors/s, batched FP32 vs plain FP64 at N=20; %HBM roof"
+UNIT = "states*vectors/s"
+WORKLOAD = "lattice4x5"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def algorithmic_flops_per_sv(two_s, lattice_half=True):
+    """Flops one state x vector needs per Lanczos step in the matvec, for
+    s = 1/2: every pair flip is a complex multiply-add (8 flops) except the
+    s+ s- / s- s+ terms, whose coefficient is real (4 flops) and which occur
+    for half of the pairs on average; every single-site flip is complex
+    (8 flops); the diagonal is real (2 flops); the fused epilogue (the
+    beta term, alpha and p reductions) adds 14."""
+    n = len(two_s)
+    pairs = n * (n - 1) // 2
+    return pairs * 0.5 * (4 + 8) + n * 8 + 2 + 14
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2607_25585_gb300 as F
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    F.build()
+    spec = W.WORKLOADS[WORKLOAD]
+    w = spec["system"]()
+    R, M = spec["R"], args.M or spec["M"]
+    T = W.temperatures()
+    s = F.System.from_dict(w)
+    d = s.dim
+    stream = torch.cuda.Stream()
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], vec_offset=rank * R, dtype="c64", stream=stream,
+              time_kernels=True)
+    F.run(s, autotune=True, **kw)          # tunes launch shapes, captures the graph
+    for _ in range(args.warmup):
+        F.run(s, **kw)
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    hv_ms, launches, hv_launches, results = 0.0, 0, 0, None
+    for _ in range(args.steps):
+        results = F.run(s, **kw)
+        hv_ms += results["hv_ms"]
+        launches += results["kernel_launches"]
+        hv_launches += results["hv_launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    sv_per_step = d * R * M
+    value = sv_per_step * args.steps * ws / (ms / 1e3)
+
+    # end to end through the C ABI from host inputs: create the system from
+    # host arrays, run, read the results back, destroy -- every step
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(max(1, min(args.steps, 3))):
+            s2 = F.System.from_dict(w)
+            r2 = F.run(s2, R=R, M=M, T=T, seed=spec["seed"], vec_offset=rank * R, dtype="c64")
+            h2d += s2.table_bytes + r2["h2d_bytes"]
+            d2h += r2["d2h_bytes"]
+            s2.close()
+        n_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": sv_per_step * n_e2e * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d / n_e2e),
+               "d2h_bytes_per_step": int(d2h / n_e2e), "steps": n_e2e}
+
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6778.0)
+    line = None
+    if rank == 0:
+        # dominant kernel: the fused H.v + Lanczos epilogue
+        hv_per_launch_ms = hv_ms / max(1, hv_launches)
+        flops_sv = algorithmic_flops_per_sv(w["two_s"])
+        achieved = flops_sv * d * R / (hv_per_launch_ms / 1e3) / 1e12
+        sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic_lattice4x5.json")
+        if os.path.exists(tf):
+            try:
+                traffic = json.load(open(tf)).get("bytes_per_launch")
+            except Exception:
+                traffic = None
+        plain = None if args.no_plain else plain_fp64(F, s, T, spec, stream, args)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"open 4x5 s=1/2 lattice, all-pairs dipolar, d={d}, R={R} vectors, M={M} "
+                                   "Lanczos steps, complex64 vectors, FP32 matvec, FP64 scalars/eigensolve/sums",
+                       "d": d, "R": R, "M": M, "global_batch_vectors": R * ws, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (three 512 MB vector blocks)"},
+            "hbm_roof_frac": value / ws * 32 / (hbm * 1e9),
+            "roofline": {"bound": "alu", "kernel": "rows_kernel<float,2,Lanczos> (fused H.v step)",
+                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": traffic, "algorithmic_flops_per_sv": flops_sv,
+                         "hv_ms_per_launch": hv_per_launch_ms,
+                         "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"},
+            "hbm": {"bytes_per_sv": 32, "peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                    "frac": value / ws * 32 / (hbm * 1e9)},
+            "plain_fp64": plain,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+        }
+        if plain and plain.get("value"):
+            line["speedup_vs_plain_fp64"] = value / ws / plain["value"]
+        if args.cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(args)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def plain_fp64(F, s, T, spec, stream, args):
+    """The plain FP64 GPU path: complex128, one Lanczos chain at a time (R = 1),
+    same gather kernels; timed on a bounded sample of chains."""
+    import torch
+    d = s.dim
+    M = args.M or spec["M"]
+    chains = args.plain_chains
+    kw = dict(R=1, M=M, T=T, seed=spec["seed"], dtype="c128", stream=stream)
+    F.run(s, autotune=True, **kw)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for c in range(chains):
+        F.run(s, vec_offset=c, **kw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return {"value": d * M * chains / (ms / 1e3), "unit": UNIT, "chains": chains, "M": M,
+            "sample": f"{chains} complex128 chains (R=1) x {M} steps on the same system"}
+
+
+def cpu_baseline(args, steps=None):
+    """The oracle as it stands on the host cores: R = #threads vectors x a few
+    Lanczos steps of the same workload."""
+    import oracle
+    oracle.build()
+    spec = W.WORKLOADS[WORKLOAD]
+    w = spec["system"]()
+    s = oracle.System(**{k: v for k, v in w.items() if k != "name"})
+    cores = oracle.num_threads()
+    M = args.cpu_steps
+    t0 = time.perf_counter()
+    oracle.ftlm(s, R=cores, M=M, T=W.temperatures(), seed=spec["seed"])
+    dt = time.perf_counter() - t0
+    return {"value": s.dim * cores * M / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} vectors x {M} Lanczos steps of the full d={s.dim} system "
+                      f"(plain C++ FP64 oracle, OpenMP over vectors), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    spec = W.WORKLOADS[WORKLOAD]
+    w = spec["system"]()
+    s = oracle.System(**{k: v for k, v in w.items() if k != "name"})
+    cores = oracle.num_threads()
+    M = args.cpu_steps
+    T = W.temperatures()
+    for _ in range(args.warmup):
+        oracle.ftlm(s, R=cores, M=1, T=T, seed=spec["seed"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.ftlm(s, R=cores, M=M, T=T, seed=spec["seed"])
+    dt = time.perf_counter() - t0
+    value = s.dim * cores * M * args.steps / dt
+    sample = (f"each step: {cores} vectors x {M} Lanczos steps of the full d={s.dim} system "
+              "(plain C++ FP64 oracle, OpenMP over vectors)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "open 4x5 s=1/2 lattice, all-pairs dipolar, d=1048576 (oracle sample)",
+                       "R": cores, "M": M},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--M", type=int, default=0, help="Lanczos steps per run (default: the workload's 200)")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="Lanczos steps of the oracle sample")
+    ap.add_argument("--plain-chains", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,897 @@
+// C ABI of the FTLM library (include/ftlm.h): system objects, the H.v, u.S
+// and start-block entry points, and the FTLM driver (arxiv 2607.25585,
+// Eqs. 4-5 and Sec. II.C): start block, M Lanczos steps captured in one CUDA
+// graph, then the host eigensolve and Boltzmann sums.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ftlm_internal.h"
+
+using namespace ftlm;
+
+namespace {
+
+thread_local std::string g_err;
+
+ftlm_status fail(ftlm_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e__ = (call);                                                                     \
+    if (e__ != cudaSuccess) {                                                                     \
+      cudaGetLastError();                                                                         \
+      return fail(e__ == cudaErrorMemoryAllocation ? FTLM_ERR_OUT_OF_MEMORY : FTLM_ERR_CUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e__));                           \
+    }                                                                                             \
+  } while (0)
+
+#define CKI(expr)                                                                                  \
+  do {                                                                                             \
+    int e__ = (expr);                                                                              \
+    if (e__ != 0) {                                                                                \
+      cudaGetLastError();                                                                          \
+      return fail(FTLM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString((cudaError_t)e__)); \
+    }                                                                                              \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (bytes >= b && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    else p = nullptr;
+    return e;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// system object
+// ---------------------------------------------------------------------------
+struct ftlm_system {
+  HostSystem hs;
+  int device = 0;
+  DevBuf tab_f, tab_d;   // coupling tables, float and double
+  DevBuf stride, q;
+  cudaStream_t own_stream = nullptr;  // runs capture and launch their graphs here
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // order own_stream after / before the caller's stream
+  uint64_t id = 0;       // unique per system
+  uint64_t gen = 0;      // bumped whenever the workspace is reallocated
+  DevBuf A, B, U, scal;  // Lanczos workspace: two vector blocks, the observable block, scalars
+  DevBuf ep, ecnt, esc;  // start-block scratch: partials, arrival counter, scalars
+  std::mutex mu;
+};
+
+namespace {
+
+std::mutex g_mu;
+uint64_t g_next_id = 1;
+size_t g_prepared_smem = 0;
+
+// Asynchronous entry points run on the caller's stream; NULL is the CUDA
+// default (legacy) stream.
+cudaStream_t pick_stream(const ftlm_system*, void* st) { return reinterpret_cast<cudaStream_t>(st); }
+
+int vchunk(int c64, int R) { return (c64 && R % 2 == 0) ? 2 : 1; }
+int max_vectors(int c64) { return c64 ? 512 : 256; }
+
+ftlm_status prepare_smem(size_t smem) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (smem <= g_prepared_smem) return FTLM_OK;
+  CKI(prepare_rows_kernels(smem));
+  g_prepared_smem = smem;
+  return FTLM_OK;
+}
+
+// ---- launch shapes and the autotuner ----------------------------------------
+
+struct ShapeKey {
+  int n, qmax, R, c64;
+  long long dim;
+  bool operator<(const ShapeKey& o) const {
+    return std::tie(n, qmax, R, c64, dim) < std::tie(o.n, o.qmax, o.R, o.c64, o.dim);
+  }
+};
+std::map<ShapeKey, Shape> g_shapes;
+
+Shape shape_for(int R, int c64, int threads_target, int tile_factor) {
+  const int V = vchunk(c64, R);
+  const int C = R / V;
+  Shape sh;
+  sh.threads = C * std::max(1, threads_target / C);
+  const int rows_pass = sh.threads / C;
+  int rows = std::max(rows_pass, (16384 / std::max(1, R)) * tile_factor);
+  sh.rows_per_tile = ((rows + rows_pass - 1) / rows_pass) * rows_pass;
+  sh.ctas_per_sm = 0;  // from the occupancy calculator
+  return sh;
+}
+
+Shape default_shape(int R, int c64) { return shape_for(R, c64, 256, 1); }
+
+InstDesc base_desc(const ftlm_system* s, int c64) {
+  InstDesc d;
+  const HostSystem& hs = s->hs;
+  d.tab = c64 ? s->tab_f.p : s->tab_d.p;
+  d.stride = reinterpret_cast<const long long*>(s->stride.p);
+  d.q = reinterpret_cast<const int*>(s->q.p);
+  d.dim = (long long)hs.dim;
+  d.n = hs.n;
+  d.all_half = hs.all_half ? 1 : 0;
+  d.lay = hs.lay;
+  return d;
+}
+
+struct HalfPlan {
+  bool on = false;
+  int K = 3, Rg = 1, threads = 256, rows_per_tile = 0, grid = 0, nvg = 0, tiles_per_vg = 0;
+  size_t smem = 0;
+};
+
+struct Plan {
+  int c64 = 0, R = 0, V = 1, C = 1;
+  Shape sh;
+  int grid = 0;
+  size_t smem = 0;
+  LaunchArgs base;
+  std::vector<int> tile_start;
+  HalfPlan half;  // spin-1/2 kernel for the H.v modes, when applicable
+};
+
+int largest_divisor_at_most(int R, int cap) {
+  for (int g = std::min(R, cap); g >= 1; --g)
+    if (R % g == 0) return g;
+  return 1;
+}
+
+// Spin-1/2 register-cube launch: K cube bits, Rg vectors per group, tile of
+// rows_factor cubes per slot.
+bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_factor, HalfPlan& h) {
+  const HostSystem& hs = s->hs;
+  if (!hs.all_half || hs.n < K + 2 || K < 2 || K > 4 || Rg < 1 || Rg > R) return false;
+  h = HalfPlan();
+  h.K = K;
+  h.Rg = Rg;
+  const int slots = std::max(1, 256 / Rg);
+  h.threads = slots * Rg;
+  long long rows = (long long)slots * (1ll << K) * rows_factor;
+  rows = std::min<long long>(rows, (long long)hs.dim);
+  rows = std::max<long long>(rows, 1ll << K);
+  h.rows_per_tile = (int)rows;
+  h.nvg = (R + Rg - 1) / Rg;
+  h.tiles_per_vg = (int)((long long)hs.dim / rows);
+  const long long ntiles = (long long)h.tiles_per_vg * h.nvg;
+  if (ntiles > (1ll << 30)) return false;
+  h.smem = half_smem_bytes(hs.n, K, h.rows_per_tile, h.threads);
+  if (h.smem > 200 * 1024) return false;
+  if (prepare_half_kernels(std::max<size_t>(h.smem, 48 * 1024)) != 0) return false;
+  const int per_sm = half_max_ctas_per_sm(K, c64, h.threads, h.smem);
+  h.grid = (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)std::max(1, device_sm_count()) * per_sm));
+  h.on = true;
+  return true;
+}
+
+ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan& pl, const Shape* force = nullptr) {
+  pl.c64 = c64;
+  pl.R = R;
+  pl.V = vchunk(c64, R);
+  pl.C = R / pl.V;
+  const ftlm_system* big = sys[0];
+  for (auto* s : sys)
+    if (s->hs.dim > big->hs.dim) big = s;
+  if (force) {
+    pl.sh = *force;
+  } else {
+    ShapeKey key{big->hs.n, big->hs.qmax, R, c64, (long long)big->hs.dim};
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_shapes.find(key);
+    pl.sh = it != g_shapes.end() ? it->second : default_shape(R, c64);
+  }
+  LaunchArgs a;
+  a.R = R;
+  a.C = pl.C;
+  a.rows_per_tile = pl.sh.rows_per_tile;
+  int tab = 0, maxn = 0;
+  pl.tile_start.assign(1, 0);
+  for (auto* s : sys) {
+    tab = std::max(tab, s->hs.lay.total);
+    maxn = std::max(maxn, s->hs.n);
+    const long long tiles = ((long long)s->hs.dim + a.rows_per_tile - 1) / a.rows_per_tile;
+    if (pl.tile_start.back() + tiles > (1ll << 30)) return fail(FTLM_ERR_UNSUPPORTED, "too many tiles");
+    pl.tile_start.push_back(pl.tile_start.back() + (int)tiles);
+  }
+  a.tab_reals = tab;
+  a.max_n = maxn;
+  a.n_inst = (int)sys.size();
+  a.ntiles = pl.tile_start.back();
+  pl.smem = rows_smem_bytes(a, c64, pl.sh.threads);
+  if (pl.smem > 227 * 1024) return fail(FTLM_ERR_UNSUPPORTED, "coupling tables do not fit in shared memory");
+  ftlm_status ps = prepare_smem(std::max<size_t>(pl.smem, 48 * 1024));
+  if (ps != FTLM_OK) return ps;
+  const int per_sm = pl.sh.ctas_per_sm > 0 ? pl.sh.ctas_per_sm : rows_max_ctas_per_sm(c64, pl.sh.threads, pl.smem, 0);
+  const int sms = std::max(1, device_sm_count());
+  pl.grid = std::max(1, std::min(a.ntiles, sms * per_sm));
+  pl.base = a;
+  pl.half.on = false;
+  if (sys.size() == 1 && pl.sh.half_K > 0)
+    make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.half);
+  else if (sys.size() == 1 && !force && !pl.sh.explicit_general && sys[0]->hs.all_half)
+    make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 16), 2, pl.half);
+  return FTLM_OK;
+}
+
+// Launches one mode of the plan: the spin-1/2 kernel for H.v modes when the
+// plan has it, the general row kernel otherwise.
+int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
+  if (pl.half.on && (a.mode == kModeApply || a.mode == kModeLanczos)) {
+    a.rows_per_tile = pl.half.rows_per_tile;
+    a.Rg = pl.half.Rg;
+    a.nvg = pl.half.nvg;
+    a.tiles_per_vg = pl.half.tiles_per_vg;
+    a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
+    return launch_half(a, pl.half.K, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+  }
+  return launch_rows(a, pl.c64, pl.grid, pl.sh.threads, pl.smem, st);
+}
+
+int plan_max_grid(const Plan& pl) { return std::max(pl.grid, pl.half.on ? pl.half.grid : 0); }
+
+// ---- workspace ----------------------------------------------------------------
+
+size_t scalar_bytes(int R, int M) {
+  return sizeof(double) * ((size_t)M * R * 4 + (size_t)(M + 1) * R + R) + sizeof(int) * 2 * (size_t)R + 64;
+}
+
+ftlm_status ensure_workspace(ftlm_system* s, int R, int M, int c64) {
+  const size_t block = (size_t)s->hs.dim * R * (c64 ? 8 : 16);
+  if (s->A.bytes < block || s->scal.bytes < scalar_bytes(R, M)) {
+    s->A.release();
+    s->B.release();
+    s->U.release();
+    s->scal.release();
+    CK(s->A.ensure(block));
+    CK(s->B.ensure(block));
+    CK(s->U.ensure(block));
+    CK(s->scal.ensure(scalar_bytes(R, M)));
+    s->gen++;
+  }
+  return FTLM_OK;
+}
+
+DevScalars scalars_at(void* base, int R, int M) {
+  DevScalars sc;
+  double* b = reinterpret_cast<double*>(base);
+  sc.alpha = b;
+  b += (size_t)M * R;
+  sc.beta = b;
+  b += (size_t)M * R;
+  sc.p = b;
+  b += (size_t)M * R * 2;
+  sc.sigma = b;
+  b += (size_t)(M + 1) * R;
+  sc.scale = b;
+  b += R;
+  int* ib = reinterpret_cast<int*>(b);
+  sc.active = ib;
+  sc.meff = ib + R;
+  return sc;
+}
+
+// ---- captured runs ------------------------------------------------------------
+
+struct RunCtx {
+  std::string key;
+  std::vector<uint64_t> deps;  // system ids
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  DevBuf desc, tiles, partials, counter;
+  std::vector<cudaEvent_t> ev;  // [2M + 2] when kernel timing is on
+  int launches = 0, hv_launches = 0;
+  char* pinned = nullptr;
+  size_t h2d = 0;
+  ~RunCtx() {
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    desc.release();
+    tiles.release();
+    partials.release();
+    counter.release();
+    for (auto e : ev) cudaEventDestroy(e);
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+
+std::vector<std::unique_ptr<RunCtx>> g_ctx;  // small cache of captured runs, newest last
+
+void purge_ctx_of(uint64_t id) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_ctx.begin(); it != g_ctx.end();) {
+    bool hit = false;
+    for (auto d : (*it)->deps) hit = hit || d == id;
+    if (hit) it = g_ctx.erase(it);
+    else ++it;
+  }
+}
+
+std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params* p, const Plan& pl) {
+  char buf[640];
+  std::string k;
+  for (auto* s : sys) {
+    snprintf(buf, sizeof buf, "%llu:%llu,", (unsigned long long)s->id, (unsigned long long)s->gen);
+    k += buf;
+  }
+  double u[3];
+  observable_coefs(sys[0]->hs, p->obs_dir, u);
+  snprintf(buf, sizeof buf,
+           "|R%d M%d dt%d seed%llu off%llu st%d bo%llu us%p tk%d th%d rpt%d g%d tol%.17g obs%.17g,%.17g,%.17g,%d s%p",
+           p->R, p->M, (int)p->dtype, (unsigned long long)p->seed, (unsigned long long)p->vec_offset, p->start,
+           (unsigned long long)p->basis_offset, p->user_start, p->time_kernels, pl.sh.threads, pl.sh.rows_per_tile,
+           pl.grid, p->breakdown_tol, u[0], u[1], u[2], p->obs_dir ? 1 : 0, p->stream);
+  k += buf;
+  snprintf(buf, sizeof buf, "|half%d K%d Rg%d rpt%d g%d", pl.half.on ? 1 : 0, pl.half.K, pl.half.Rg,
+           pl.half.rows_per_tile, pl.half.grid);
+  return k + buf;
+}
+
+ftlm_status validate_params(const ftlm_run_params* p, const std::vector<ftlm_system*>& sys) {
+  if (!p) return fail(FTLM_ERR_INVALID_ARG, "params is NULL");
+  if (p->dtype != FTLM_C64 && p->dtype != FTLM_C128) return fail(FTLM_ERR_INVALID_ARG, "unknown dtype");
+  const int c64 = p->dtype == FTLM_C64;
+  if (p->R < 1 || p->R > max_vectors(c64))
+    return fail(FTLM_ERR_INVALID_ARG, "R must be in 1.." + std::to_string(max_vectors(c64)));
+  if (p->M < 1 || p->M > 100000) return fail(FTLM_ERR_INVALID_ARG, "M must be in 1..100000");
+  if (!p->T || p->nT < 1) return fail(FTLM_ERR_INVALID_ARG, "temperature grid missing");
+  for (int t = 0; t < p->nT; ++t)
+    if (!(p->T[t] > 0.0) || !std::isfinite(p->T[t])) return fail(FTLM_ERR_INVALID_ARG, "temperatures must be > 0");
+  if (p->start < 0 || p->start > 2) return fail(FTLM_ERR_INVALID_ARG, "unknown start mode");
+  if (p->start == FTLM_START_USER && !p->user_start) return fail(FTLM_ERR_INVALID_ARG, "user_start is NULL");
+  if (p->start == FTLM_START_USER && (reinterpret_cast<uintptr_t>(p->user_start) & 15))
+    return fail(FTLM_ERR_INVALID_ARG, "user_start must be 16-byte aligned");
+  if (p->start == FTLM_START_USER && sys.size() != 1)
+    return fail(FTLM_ERR_INVALID_ARG, "user start vectors need a single system");
+  if (!(p->breakdown_tol >= 0) || !std::isfinite(p->breakdown_tol))
+    return fail(FTLM_ERR_INVALID_ARG, "breakdown_tol must be finite and >= 0");
+  if (p->obs_dir && !(std::isfinite(p->obs_dir[0]) && std::isfinite(p->obs_dir[1]) && std::isfinite(p->obs_dir[2])))
+    return fail(FTLM_ERR_INVALID_ARG, "obs_dir must be finite");
+  for (auto* s : sys) {
+    if (!s) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
+    if (p->start == FTLM_START_BASIS && p->basis_offset + (uint64_t)p->R > s->hs.dim)
+      return fail(FTLM_ERR_INVALID_ARG, "basis_offset + R exceeds the dimension");
+  }
+  return FTLM_OK;
+}
+
+size_t staged_bytes(int R, int M) { return sizeof(double) * ((size_t)M * R * 4) + sizeof(int) * (size_t)R; }
+
+// Enqueues one whole run on `st` (which the caller is capturing).
+ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const ftlm_run_params* p, const Plan& pl,
+                        cudaStream_t st) {
+  const int M = p->M, R = p->R, c64 = pl.c64;
+  const int n = (int)sys.size();
+  const InstDesc* d_even = reinterpret_cast<const InstDesc*>(ctx.desc.p);
+  const InstDesc* d_odd = d_even + n;
+  const InstDesc* d_start = d_even + 2 * n;
+  LaunchArgs a = pl.base;
+  a.tile_start = reinterpret_cast<const int*>(ctx.tiles.p);
+  a.partials = reinterpret_cast<double*>(ctx.partials.p);
+  a.counter = reinterpret_cast<unsigned*>(ctx.counter.p);
+  ctx.launches = 0;
+  ctx.hv_launches = 0;
+  const bool tk = p->time_kernels != 0;
+  int evi = 0;
+  if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+  for (int k = 0; k < n; ++k) {  // start block -> A
+    InstDesc h = base_desc(sys[k], c64);
+    if (p->start == FTLM_START_RANDOM)
+      CKI(launch_start_random(&h, nullptr, R, p->seed, p->vec_offset, sys[k]->A.p, c64, st));
+    else if (p->start == FTLM_START_BASIS)
+      CKI(launch_start_basis((long long)sys[k]->hs.dim, R, p->basis_offset, sys[k]->A.p, c64, st));
+    else
+      CKI(launch_copy_block(p->user_start, sys[k]->A.p, (size_t)sys[k]->hs.dim * R * (c64 ? 8 : 16), st));
+    ctx.launches++;
+  }
+  a.inst = d_start;  // sigma_0 = 1/|q_0|, then U = sigma_0 (u.S) q_0
+  a.mode = kModeStartNorm;
+  CKI(launch_plan(pl, a, st));
+  a.mode = kModeApplyS;
+  a.use_sigma0 = 1;
+  CKI(launch_plan(pl, a, st));
+  a.use_sigma0 = 0;
+  ctx.launches += 2;
+  for (int j = 0; j < M; ++j) {
+    a.inst = (j % 2 == 0) ? d_even : d_odd;
+    a.step = j;
+    a.first = j == 0;
+    a.mode = kModeLanczos;
+    if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+    CKI(launch_plan(pl, a, st));
+    if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+    a.mode = kModeUpdate;
+    CKI(launch_plan(pl, a, st));
+    ctx.launches += 2;
+    ctx.hv_launches++;
+  }
+  if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+  const size_t per = staged_bytes(R, M);
+  for (int k = 0; k < n; ++k) {  // alpha, beta, p, M_eff -> pinned host staging
+    DevScalars sc = scalars_at(sys[k]->scal.p, R, M);
+    char* dst = ctx.pinned + per * k;
+    CK(cudaMemcpyAsync(dst, sc.alpha, sizeof(double) * (size_t)M * R * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dst + sizeof(double) * (size_t)M * R * 4, sc.meff, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  }
+  return FTLM_OK;
+}
+
+ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftlm_run_params* p, const Plan& pl,
+                      cudaStream_t st) {
+  const int c64 = pl.c64, R = p->R, M = p->M, n = (int)sys.size();
+  for (auto* s : sys) c.deps.push_back(s->id);
+  // descriptors: even steps (x = A, y = B), odd steps (x = B, y = A), start (x = A, y = U)
+  std::vector<InstDesc> h(3 * n);
+  for (int k = 0; k < n; ++k) {
+    ftlm_system* s = sys[k];
+    InstDesc d = base_desc(s, c64);
+    d.sc = scalars_at(s->scal.p, R, M);
+    d.u = s->U.p;
+    d.M = M;
+    d.tol = p->breakdown_tol > 0 ? p->breakdown_tol : (c64 ? 1e-6 : 1e-12);
+    observable_coefs(s->hs, p->obs_dir, d.obs);  // per instance: each system has its own field direction
+    InstDesc e = d, o = d, t = d;
+    e.x = s->A.p;
+    e.y = s->B.p;
+    o.x = s->B.p;
+    o.y = s->A.p;
+    t.x = s->A.p;
+    t.y = s->U.p;
+    h[k] = e;
+    h[n + k] = o;
+    h[2 * n + k] = t;
+  }
+  CK(c.desc.ensure(sizeof(InstDesc) * h.size()));
+  CK(cudaMemcpy(c.desc.p, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice));
+  CK(c.tiles.ensure(sizeof(int) * pl.tile_start.size()));
+  CK(cudaMemcpy(c.tiles.p, pl.tile_start.data(), sizeof(int) * pl.tile_start.size(), cudaMemcpyHostToDevice));
+  CK(c.partials.ensure(sizeof(double) * (size_t)n * plan_max_grid(pl) * R * kNumPartials));
+  CK(c.counter.ensure(64));
+  CK(cudaMemset(c.counter.p, 0, 64));
+  c.h2d = sizeof(InstDesc) * h.size() + sizeof(int) * pl.tile_start.size();
+  CK(cudaMallocHost(reinterpret_cast<void**>(&c.pinned), staged_bytes(R, M) * n));
+  if (p->time_kernels) {
+    c.ev.resize(2 * M + 2);
+    for (auto& e : c.ev) CK(cudaEventCreate(&e));
+  }
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  ftlm_status es = enqueue_run(c, sys, p, pl, st);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(st, &g);
+  if (es != FTLM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return es;
+  }
+  CK(ce);
+  c.g = g;
+  CK(cudaGraphInstantiate(&c.ex, g, 0));
+  return FTLM_OK;
+}
+
+ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ftlm_result* res) {
+  ftlm_status vs = validate_params(p, sys);
+  if (vs != FTLM_OK) return vs;
+  if (!res) return fail(FTLM_ERR_INVALID_ARG, "result is NULL");
+  const int c64 = p->dtype == FTLM_C64;
+  const int R = p->R, M = p->M, n = (int)sys.size();
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  for (auto* s : sys)
+    if (s->device != dev) return fail(FTLM_ERR_INVALID_ARG, "system lives on another device");
+  const cudaStream_t caller = pick_stream(sys[0], p->stream);
+  const cudaStream_t st = sys[0]->own_stream;  // graphs are captured and launched on the first system's stream
+  for (auto* s : sys) {
+    ftlm_status w = ensure_workspace(s, R, M, c64);
+    if (w != FTLM_OK) return w;
+  }
+  Plan pl;
+  ftlm_status ps = make_plan(sys, R, c64, pl);
+  if (ps != FTLM_OK) return ps;
+  const std::string key = run_key(sys, p, pl);
+  RunCtx* ctx = nullptr;
+  size_t h2d = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& c : g_ctx)
+      if (c->key == key) ctx = c.get();
+  }
+  if (!ctx) {
+    auto nc = std::make_unique<RunCtx>();
+    nc->key = key;
+    ftlm_status bs = build_ctx(*nc, sys, p, pl, st);
+    if (bs != FTLM_OK) return bs;
+    h2d = nc->h2d;
+    ctx = nc.get();
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_ctx.push_back(std::move(nc));
+    if (g_ctx.size() > 8) g_ctx.erase(g_ctx.begin());
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaEventRecord(sys[0]->ev_in, caller));  // after the caller's prior work (e.g. a user start block)
+  CK(cudaStreamWaitEvent(st, sys[0]->ev_in, 0));
+  CK(cudaGraphLaunch(ctx->ex, st));
+  CK(cudaEventRecord(sys[0]->ev_out, st));
+  CK(cudaStreamWaitEvent(caller, sys[0]->ev_out, 0));  // the caller's later work sees the run complete
+  CK(cudaStreamSynchronize(st));
+  const auto t1 = std::chrono::steady_clock::now();
+  double hv_ms = 0.0, dev_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  if (p->time_kernels && !ctx->ev.empty()) {
+    for (int j = 0; j < M; ++j) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[1 + 2 * j], ctx->ev[2 + 2 * j]));
+      hv_ms += ms;
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2 * M + 1]));
+    dev_ms = ms;
+  }
+  const size_t per = staged_bytes(R, M);
+  for (int k = 0; k < n; ++k) {  // host: eigensolve + sums per instance
+    const char* src = ctx->pinned + per * k;
+    const double* alpha_d = reinterpret_cast<const double*>(src);  // [M][R]
+    const double* beta_d = alpha_d + (size_t)M * R;
+    const double* p_d = beta_d + (size_t)M * R;                     // [M][R][2]
+    const int* meff = reinterpret_cast<const int*>(src + sizeof(double) * (size_t)M * R * 4);
+    std::vector<double> al((size_t)R * M), be((size_t)R * M), pp((size_t)R * M * 2);
+    for (int r = 0; r < R; ++r)
+      for (int j = 0; j < M; ++j) {
+        al[(size_t)r * M + j] = alpha_d[(size_t)j * R + r];
+        be[(size_t)r * M + j] = beta_d[(size_t)j * R + r];
+        pp[((size_t)r * M + j) * 2] = p_d[((size_t)j * R + r) * 2];
+        pp[((size_t)r * M + j) * 2 + 1] = p_d[((size_t)j * R + r) * 2 + 1];
+      }
+    std::vector<int> me(meff, meff + R);
+    for (int r = 0; r < R; ++r)
+      if (me[r] < 1 || me[r] > M) return fail(FTLM_ERR_NUMERICAL, "start vector of zero norm");
+    ftlm_result& out = res[k];
+    std::string msg;
+    ftlm_status ss = host_sums(R, M, me.data(), al.data(), be.data(), pp.data(), (double)sys[k]->hs.dim,
+                               sys[k]->hs.g, p->T, p->nT, &out, msg);
+    if (ss != FTLM_OK) return fail(ss, msg);
+    if (out.alpha) std::memcpy(out.alpha, al.data(), sizeof(double) * al.size());
+    if (out.beta) std::memcpy(out.beta, be.data(), sizeof(double) * be.size());
+    if (out.p) std::memcpy(out.p, pp.data(), sizeof(double) * pp.size());
+    if (out.M_eff) std::memcpy(out.M_eff, me.data(), sizeof(int) * R);
+    out.device_ms = dev_ms;
+    out.hv_ms = hv_ms;
+    out.hv_launches = ctx->hv_launches;
+    out.kernel_launches = ctx->launches;
+    out.h2d_bytes = k == 0 ? h2d : 0;
+    out.d2h_bytes = per;
+  }
+  return FTLM_OK;
+}
+
+// Times candidate launch shapes of the H.v kernel on the system's workspace
+// and keeps the fastest for (n, 2s+1, R, dtype, d).
+ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
+  ShapeKey key{s->hs.n, s->hs.qmax, R, c64, (long long)s->hs.dim};
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_shapes.count(key)) return FTLM_OK;
+  }
+  std::vector<Shape> cands;
+  if (s->hs.all_half && s->hs.n >= 4) {
+    std::vector<int> rgs;
+    for (int cap : {16, 8, 4}) {
+      const int g = largest_divisor_at_most(R, cap);
+      if (std::find(rgs.begin(), rgs.end(), g) == rgs.end()) rgs.push_back(g);
+    }
+    for (int K : {2, 3, 4})
+      for (int rg : rgs)
+        for (int f : {1, 4}) {  // cubes per thread slot in a row tile
+          Shape sh = default_shape(R, c64);
+          sh.half_K = K;
+          sh.Rg = rg;
+          sh.half_rows = f;
+          if (s->hs.n >= K + 2) cands.push_back(sh);
+        }
+  } else {
+    for (int thr : {128, 256})
+      for (int f : {1, 4}) cands.push_back(shape_for(R, c64, thr, f));
+  }
+  ftlm_status w = ensure_workspace(s, R, 1, c64);
+  if (w != FTLM_OK) return w;
+  CK(cudaMemsetAsync(s->A.p, 0, (size_t)s->hs.dim * R * (c64 ? 8 : 16), st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Shape pick = default_shape(R, c64);
+  std::vector<ftlm_system*> one{s};
+  for (const Shape& sh : cands) {
+    Plan pl;
+    if (make_plan(one, R, c64, pl, &sh) != FTLM_OK) continue;
+    if (sh.half_K > 0 && !pl.half.on) continue;
+    LaunchArgs a = pl.base;
+    a.inline_one = 1;
+    a.one = base_desc(s, c64);
+    a.one.x = s->A.p;
+    a.one.y = s->B.p;
+    a.mode = kModeApply;
+    CKI(launch_plan(pl, a, st));  // warm-up
+    CK(cudaEventRecord(e0, st));
+    for (int it = 0; it < 3; ++it) CKI(launch_plan(pl, a, st));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = sh;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_shapes[key] = pick;
+  return FTLM_OK;
+}
+
+ftlm_status check_block_args(const ftlm_system* s, const void* x, const void* y, int nvec, ftlm_dtype dtype) {
+  if (!s) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
+  if (dtype != FTLM_C64 && dtype != FTLM_C128) return fail(FTLM_ERR_INVALID_ARG, "unknown dtype");
+  const int c64 = dtype == FTLM_C64;
+  if (nvec < 1 || nvec > max_vectors(c64))
+    return fail(FTLM_ERR_INVALID_ARG, "nvec must be in 1.." + std::to_string(max_vectors(c64)));
+  if (!x || !y) return fail(FTLM_ERR_INVALID_ARG, "vector blocks must not be NULL");
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+    return fail(FTLM_ERR_INVALID_ARG, "vector blocks must be 16-byte aligned");
+  return FTLM_OK;
+}
+
+ftlm_status rows_entry(const ftlm_system* cs, int mode, const double* u, const void* x, void* y, int nvec,
+                       ftlm_dtype dtype, void* stream) {
+  ftlm_status v = check_block_args(cs, x, y, nvec, dtype);
+  if (v != FTLM_OK) return v;
+  const int c64 = dtype == FTLM_C64;
+  ftlm_system* s = const_cast<ftlm_system*>(cs);
+  const size_t bytes = (size_t)s->hs.dim * nvec * (c64 ? 8 : 16);
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+  if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
+  Plan pl;
+  std::vector<ftlm_system*> one{s};
+  ftlm_status ps = make_plan(one, nvec, c64, pl);
+  if (ps != FTLM_OK) return ps;
+  LaunchArgs a = pl.base;
+  a.inline_one = 1;
+  a.one = base_desc(s, c64);
+  a.one.x = x;
+  a.one.y = y;
+  a.mode = mode;
+  observable_coefs(s->hs, u, a.one.obs);
+  CKI(launch_plan(pl, a, pick_stream(s, stream)));
+  return FTLM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+ftlm_status ftlm_system_create(int n_sites, const int* two_s, const double* J, const double* d_ion,
+                               const double* e_axes, double g, const double B[3], const double* pos,
+                               const ftlm_constants* k, ftlm_system** out) {
+  if (!out) return fail(FTLM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string msg;
+  auto s = std::make_unique<ftlm_system>();
+  ftlm_status st = build_host_system(n_sites, two_s, J, d_ion, e_axes, g, B, pos, k, s->hs, msg);
+  if (st != FTLM_OK) return fail(st, msg);
+  CK(cudaGetDevice(&s->device));
+  CK(cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    s->id = g_next_id++;
+  }
+  const HostSystem& hs = s->hs;
+  std::vector<float> tf(hs.tab.begin(), hs.tab.end());
+  std::vector<long long> stv(hs.stride.begin(), hs.stride.end());
+  cudaError_t e = s->tab_d.ensure(hs.tab.size() * sizeof(double));
+  if (e == cudaSuccess) e = s->tab_f.ensure(tf.size() * sizeof(float));
+  if (e == cudaSuccess) e = s->stride.ensure(stv.size() * sizeof(long long));
+  if (e == cudaSuccess) e = s->q.ensure(hs.q.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(s->tab_d.p, hs.tab.data(), hs.tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->tab_f.p, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->stride.p, stv.data(), stv.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->q.p, hs.q.data(), hs.q.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->tab_d.release();
+    s->tab_f.release();
+    s->stride.release();
+    s->q.release();
+    cudaEventDestroy(s->ev_in);
+    cudaEventDestroy(s->ev_out);
+    cudaStreamDestroy(s->own_stream);
+    return fail(e == cudaErrorMemoryAllocation ? FTLM_ERR_OUT_OF_MEMORY : FTLM_ERR_CUDA,
+                std::string("uploading the coupling tables: ") + cudaGetErrorString(e));
+  }
+  *out = s.release();
+  return FTLM_OK;
+}
+
+void ftlm_system_destroy(ftlm_system* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();  // the system's buffers may be in use on any stream
+  purge_ctx_of(s->id);
+  for (DevBuf* b : {&s->tab_f, &s->tab_d, &s->stride, &s->q, &s->A, &s->B, &s->U, &s->scal, &s->ep, &s->ecnt,
+                    &s->esc})
+    b->release();
+  cudaEventDestroy(s->ev_in);
+  cudaEventDestroy(s->ev_out);
+  cudaStreamDestroy(s->own_stream);
+  delete s;
+}
+
+uint64_t ftlm_system_dim(const ftlm_system* s) { return s ? s->hs.dim : 0; }
+
+uint64_t ftlm_system_table_bytes(const ftlm_system* s) {
+  if (!s) return 0;
+  return (uint64_t)s->hs.tab.size() * (sizeof(double) + sizeof(float)) +
+         (uint64_t)s->hs.n * (sizeof(long long) + sizeof(int));
+}
+
+ftlm_status ftlm_apply_h(const ftlm_system* s, const void* x, void* y, int nvec, ftlm_dtype dtype, void* stream) {
+  return rows_entry(s, kModeApply, nullptr, x, y, nvec, dtype, stream);
+}
+
+ftlm_status ftlm_apply_sdir(const ftlm_system* s, const double* u, const void* x, void* y, int nvec,
+                            ftlm_dtype dtype, void* stream) {
+  if (u && !(std::isfinite(u[0]) && std::isfinite(u[1]) && std::isfinite(u[2])))
+    return fail(FTLM_ERR_INVALID_ARG, "u must be finite");
+  return rows_entry(s, kModeApplyS, u, x, y, nvec, dtype, stream);
+}
+
+ftlm_status ftlm_start_block(const ftlm_system* cs, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                             ftlm_dtype dtype, void* stream) {
+  ftlm_status v = check_block_args(cs, out, out, nvec, dtype);
+  if (v != FTLM_OK) return v;
+  const int c64 = dtype == FTLM_C64;
+  ftlm_system* s = const_cast<ftlm_system*>(cs);
+  std::lock_guard<std::mutex> lk(s->mu);
+  cudaStream_t st = pick_stream(s, stream);
+  Plan pl;
+  std::vector<ftlm_system*> one{s};
+  ftlm_status ps = make_plan(one, nvec, c64, pl);
+  if (ps != FTLM_OK) return ps;
+  // scratch owned by the system: per-CTA partials, the arrival counter and sigma_0
+  const size_t pbytes = sizeof(double) * (size_t)pl.grid * nvec * kNumPartials;
+  if (s->ep.bytes < pbytes) CK(s->ep.ensure(pbytes));
+  if (!s->ecnt.p) {
+    CK(s->ecnt.ensure(64));
+    CK(cudaMemsetAsync(s->ecnt.p, 0, 64, st));
+  }
+  if (s->esc.bytes < scalar_bytes(nvec, 1)) CK(s->esc.ensure(scalar_bytes(nvec, 1)));
+  InstDesc h = base_desc(s, c64);
+  CKI(launch_start_random(&h, nullptr, nvec, seed, vec_offset, out, c64, st));
+  LaunchArgs a = pl.base;
+  a.inline_one = 1;
+  a.one = h;
+  a.one.x = out;
+  a.one.y = out;
+  a.one.M = 1;
+  a.one.sc = scalars_at(s->esc.p, nvec, 1);
+  a.partials = reinterpret_cast<double*>(s->ep.p);
+  a.counter = reinterpret_cast<unsigned*>(s->ecnt.p);
+  a.mode = kModeStartNorm;
+  CKI(launch_rows(a, c64, pl.grid, pl.sh.threads, pl.smem, st));
+  a.mode = kModeScale;
+  CKI(launch_rows(a, c64, pl.grid, pl.sh.threads, pl.smem, st));
+  return FTLM_OK;
+}
+
+ftlm_status ftlm_run(const ftlm_system* s, const ftlm_run_params* p, ftlm_result* res) {
+  if (!s) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
+  ftlm_system* ms = const_cast<ftlm_system*>(s);
+  std::lock_guard<std::mutex> lk(ms->mu);
+  if (p && p->autotune) {
+    ftlm_status vs = validate_params(p, {ms});
+    if (vs != FTLM_OK) return vs;
+    ftlm_status a = autotune(ms, p->R, p->dtype == FTLM_C64, pick_stream(ms, p->stream));
+    if (a != FTLM_OK) return a;
+  }
+  return run_impl({ms}, p, res);
+}
+
+ftlm_status ftlm_run_batch(int n, const ftlm_system* const* systems, const ftlm_run_params* p,
+                           ftlm_result* results) {
+  if (n < 1 || !systems || !results) return fail(FTLM_ERR_INVALID_ARG, "empty batch");
+  std::vector<ftlm_system*> v;
+  for (int k = 0; k < n; ++k) {
+    if (!systems[k]) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
+    for (auto* o : v)
+      if (o == systems[k]) return fail(FTLM_ERR_INVALID_ARG, "a system appears twice in the batch");
+    v.push_back(const_cast<ftlm_system*>(systems[k]));
+  }
+  std::vector<ftlm_system*> order = v;  // lock in address order
+  std::sort(order.begin(), order.end());
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (auto* s : order) locks.emplace_back(s->mu);
+  if (p && p->autotune) {
+    ftlm_status vs = validate_params(p, v);
+    if (vs != FTLM_OK) return vs;
+    ftlm_system* big = v[0];
+    for (auto* s : v)
+      if (s->hs.dim > big->hs.dim) big = s;
+    ftlm_status a = autotune(big, p->R, p->dtype == FTLM_C64, pick_stream(v[0], p->stream));
+    if (a != FTLM_OK) return a;
+  }
+  return run_impl(v, p, results);
+}
+
+ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, int cube_bits, int group_vectors,
+                            int tile_cubes) {
+  if (!s) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
+  if (dtype != FTLM_C64 && dtype != FTLM_C128) return fail(FTLM_ERR_INVALID_ARG, "unknown dtype");
+  const int c64 = dtype == FTLM_C64;
+  if (nvec < 1 || nvec > max_vectors(c64)) return fail(FTLM_ERR_INVALID_ARG, "nvec out of range");
+  ShapeKey key{s->hs.n, s->hs.qmax, nvec, c64, (long long)s->hs.dim};
+  if (cube_bits < 0) {  // forget the override (and any autotuned shape)
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_shapes.erase(key);
+    return FTLM_OK;
+  }
+  Shape sh = default_shape(nvec, c64);
+  sh.explicit_general = cube_bits == 0;
+  if (cube_bits != 0) {
+    if (!s->hs.all_half) return fail(FTLM_ERR_UNSUPPORTED, "register cubes need every site s = 1/2");
+    if (cube_bits < 2 || cube_bits > 4 || s->hs.n < cube_bits + 2)
+      return fail(FTLM_ERR_INVALID_ARG, "cube_bits must be 2..4 and at most n_sites - 2");
+    if (group_vectors < 1 || group_vectors > nvec || group_vectors > 256)
+      return fail(FTLM_ERR_INVALID_ARG, "group_vectors must be in 1..min(nvec, 256)");
+    if (tile_cubes < 1 || tile_cubes > 64) return fail(FTLM_ERR_INVALID_ARG, "tile_cubes must be in 1..64");
+    sh.half_K = cube_bits;
+    sh.Rg = group_vectors;
+    sh.half_rows = tile_cubes;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_shapes[key] = sh;
+  return FTLM_OK;
+}
+
+ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,
+                      double dim, double g, const double* T, int nT, ftlm_result* res) {
+  std::string msg;
+  ftlm_status s = host_sums(R, M, M_eff, alpha, beta, p, dim, g, T, nT, res, msg);
+  if (s != FTLM_OK) return fail(s, msg);
+  return FTLM_OK;
+}
+
+const char* ftlm_last_error(void) { return g_err.c_str(); }
+
+const char* ftlm_version(void) { return "ftlm-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations shared by the host driver and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ftlm.h"
+
+namespace ftlm {
+
+constexpr int kMaxSites = 64;
+constexpr int kMaxQ = 16;            // 2s + 1 <= 16
+constexpr int kNumPartials = 4;      // per vector: alpha (or |w|^2), Re p, Im p, spare
+constexpr uint64_t kMaxDim = 1ull << 36;
+
+// Layout of one system's coupling tables, in units of the table's scalar
+// type (float for the c64 path, double for c128).  Host and device compute
+// addresses from the same struct.
+struct TabLayout {
+  int n = 0, qmax = 0;
+  int off_m = 0;        // [n][qmax]  m = a - s
+  int off_up1 = 0;      // [n][qmax]  <a|s+|a-1>   (0 for a = 0)
+  int off_dn1 = 0;      // [n][qmax]  <a|s-|a+1>   (0 for a = 2s)
+  int off_up2 = 0;      // [n][qmax]  <a|s+ s+|a-2>
+  int off_dn2 = 0;      // [n][qmax]  <a|s- s-|a+2>
+  int off_iondiag = 0;  // [n][qmax]  diagonal of d_i (s_i.e_i)^2
+  int off_zz = 0;       // [n][n]     coefficient of s^z_i s^z_j (i<j, else 0)
+  int off_pm = 0;       // [n][n][2]  coefficient of s+_i s-_j (i<j)
+  int off_pp = 0;       // [n][n][2]  coefficient of s+_i s+_j (i<j)
+  int off_rho = 0;      // [n][n][2]  coefficient of s+_i s^z_j (any i != j; 0 on the diagonal)
+  int off_hp = 0;       // [n][2]     coefficient of s+_i from the Zeeman term
+  int off_bz = 0;       // [n][2]     single-ion d e_z b: multiplies (s^z s+ + s+ s^z)
+  int off_bb = 0;       // [n][2]     single-ion d b^2: multiplies s+ s+
+  int off_hz = 0;       // [n]        coefficient of s^z_i from the Zeeman term
+  int total = 0;
+};
+
+TabLayout make_layout(int n, int qmax);
+
+// Host copy of a validated system.
+struct HostSystem {
+  int n = 0;
+  std::vector<int> two_s, q;
+  std::vector<int64_t> stride;
+  uint64_t dim = 0;
+  int qmax = 0;
+  double g = 2.0;
+  double B[3] = {0, 0, 0};
+  double Bdir[3] = {0, 0, 1};
+  TabLayout lay;
+  std::vector<double> tab;  // FP64 tables in layout `lay` (u = field direction)
+  bool all_half = false;    // every site s = 1/2
+  bool real_pm = true;      // every s+ s- coefficient real (true for J + dipolar)
+};
+
+// Validates the inputs and fills `hs`.  Returns FTLM_OK or an error with `msg`.
+ftlm_status build_host_system(int n, const int* two_s, const double* J, const double* d_ion,
+                              const double* e_axes, double g, const double B[3], const double* pos,
+                              const ftlm_constants* k, HostSystem& hs, std::string& msg);
+
+// Coefficients (u_z, Re a_u, Im a_u) of the observable u.S, a_u = (u_x - i u_y)/2;
+// u = NULL selects the field direction (z when B = 0).
+void observable_coefs(const HostSystem& hs, const double* u, double out[3]);
+
+// ---- device-side descriptors ------------------------------------------------
+
+// Per-instance Lanczos scalars in device memory; arrays are [M][R] (step major).
+struct DevScalars {
+  double* alpha = nullptr;   // [M][R]
+  double* beta = nullptr;    // [M][R]   norm after step j
+  double* p = nullptr;       // [M][R][2]
+  double* sigma = nullptr;   // [M+1][R] scale: v_j = sigma_j q_j
+  double* scale = nullptr;   // [R] running max(|alpha|, beta)
+  int* active = nullptr;     // [R]
+  int* meff = nullptr;       // [R]
+};
+
+struct InstDesc {
+  const void* tab = nullptr;       // table scalars (float or double)
+  const long long* stride = nullptr;  // [n]
+  const int* q = nullptr;          // [n]
+  long long dim = 0;
+  int n = 0;
+  int all_half = 0;
+  TabLayout lay;
+  // vectors of the current launch
+  const void* x = nullptr;   // gather source (q_j), [dim][R]
+  void* y = nullptr;         // output (or in place w over q_{j-1})
+  const void* u = nullptr;   // observable vector u.S v_0, [dim][R] (Lanczos steps)
+  DevScalars sc;
+  double tol = 0.0;          // breakdown tolerance
+  int M = 0;
+  double obs[3] = {0, 0, 0}; // observable u.S: u_z, Re a_u, Im a_u with a_u = (u_x - i u_y)/2
+};
+
+enum KernelMode : int {
+  kModeApply = 0,     // y = H x
+  kModeLanczos = 1,   // w = sigma_j H q_j - beta_j sigma_{j-1} q_{j-1} (in place in y), partials alpha, p
+  kModeUpdate = 2,    // w -= alpha_j sigma_j q_j (in place in y), partials |w|^2, then beta, sigma
+  kModeStartNorm = 3, // partials |x|^2, then sigma_0 = 1/|x|
+  kModeApplyS = 4,    // y = scale * (u.S) x  (scale = sigma_0 when Lanczos)
+  kModeScale = 5,     // y = sigma_0 x (elementwise; y may equal x)
+};
+
+struct LaunchArgs {
+  const InstDesc* inst = nullptr;  // device [n_inst]; unused when inline_one
+  const int* tile_start = nullptr; // device [n_inst + 1] prefix sum of tiles per instance; unused when inline_one
+  InstDesc one;                    // the single instance, passed by value
+  int inline_one = 0;              // 1: n_inst == 1 and the descriptor is `one`
+  int n_inst = 0;
+  int ntiles = 0;
+  int rows_per_tile = 0;
+  int R = 0;
+  int C = 0;            // vector chunks per row = R / V
+  int mode = 0;
+  int step = 0;         // Lanczos step j
+  int first = 0;        // 1 at j = 0 (no beta term)
+  double* partials = nullptr;     // [n_inst][grid][R][kNumPartials]
+  unsigned* counter = nullptr;    // zeroed; reset by the last block
+  int tab_reals = 0;    // max table size over instances
+  int max_n = 0;        // max sites over instances
+  int use_sigma0 = 0;   // kModeApplyS: multiply by sigma_0
+  // spin-1/2 kernel only: vectors are processed in groups of Rg (tile order
+  // is group-major so the gathered slice stays in L2)
+  int Rg = 0;           // vectors per group
+  int nvg = 0;          // number of vector groups = ceil(R / Rg)
+  int tiles_per_vg = 0; // row tiles per vector group
+};
+
+// Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
+struct Shape {
+  int threads = 256;
+  int rows_per_tile = 256;
+  int ctas_per_sm = 2;
+  int half_K = 0;       // > 0: spin-1/2 register-cube kernel with cubes of 2^half_K rows
+  int Rg = 0;           // spin-1/2 kernel: vectors per group
+  int half_rows = 2;    // spin-1/2 kernel: cubes per thread slot in a row tile
+  bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
+};
+
+// Kernel launchers (kernels.cu).  `V` is the number of complex values per
+// thread (2 for c64, 1 for c128).  Return cudaError_t as int.
+int launch_rows(const LaunchArgs& a, int c64, int grid, int threads, size_t smem, void* stream);
+int launch_start_random(const InstDesc* inst_host, const InstDesc* inst_dev, int R, uint64_t seed,
+                        uint64_t vec_offset, void* out, int c64, void* stream);
+int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream);
+int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
+size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads);
+int prepare_rows_kernels(size_t smem);
+int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int mode);
+int device_sm_count();
+
+// Spin-1/2 register-cube kernel (hv_half.cu): modes kModeApply and kModeLanczos
+// of a single instance with every site s = 1/2.
+int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size_t smem, void* stream);
+size_t half_smem_bytes(int n, int K, int rows_per_tile, int threads);
+int prepare_half_kernels(size_t smem);
+int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem);
+
+// Host tridiagonal eigensolver + sums (tridiag.cpp).
+ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,
+                      double dim, double g, const double* T, int nT, ftlm_result* res, std::string& msg);
+
+}  // namespace ftlm

@@ -1,0 +1,402 @@
+// Spin-1/2 H.v (Eq. 3 of arxiv 2607.25585 with every s_i = 1/2): the
+// matrix-free row gather specialised to the binary basis, where every pair
+// (i, j) couples row mu to exactly one state mu ^ (e_i | e_j) and every site to
+// mu ^ e_i.
+//
+// Register cubes.  A thread owns 2^K consecutive rows (the low K bits vary)
+// of one vector.  Flips of the K cube bits stay in registers; a flip of an
+// outer bit j loads the neighbouring cube once and serves the single flip of
+// j and the K mixed pairs (c, j); an outer pair (i, j) has one coefficient for
+// the whole cube.  This cuts the gathered loads per row from N(N+1)/2 to
+// 1 + (N-K) + (N-K)(N-K-1)/2 and amortises coefficient work over 2^K rows.
+//
+// Coefficients.  Per system (once per CTA, in shared memory): the four
+// coefficients of every pair indexed by the row's two bits, the cube part of
+// the single-flip coefficients and of the diagonal.  Per row tile: the outer
+// part of the single-flip coefficients and of the diagonal for every cube.
+//
+// Vector groups.  Vectors are processed Rg at a time (tile order is
+// group-major), so the gathered slice x[:, group] (d * Rg * 8 bytes) stays in
+// L2 while all its neighbours are read.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+
+namespace ftlm {
+
+namespace {
+
+// pair index of i < j in the triangular table
+__device__ __forceinline__ int tri(int i, int j) { return (j * (j - 1)) / 2 + i; }
+
+template <typename real>
+struct HalfSmem {
+  real* cp;     // [npairs][4][2]  coefficient by (bit_i, bit_j) of the row: 0=(0,0) 1=(0,1) 2=(1,0) 3=(1,1)
+  real* fcube;  // [n][NR][2]      sum_{c<K} rho_jc m_c(r)
+  real* ecube;  // [NR]            diagonal from the cube bits alone
+  real* fhi;    // [n][Gt][2]      h+_j + sum_{i>=K} rho_ji m_i   per cube of the tile
+  real* ehi;    // [Gt]            diagonal from the outer bits alone
+  real* gz;     // [K][Gt]         sum_{i>=K} zz_ci m_i (cube-outer cross term)
+  double* red;  // [blockDim][4]
+};
+
+template <typename real>
+__device__ HalfSmem<real> half_carve(unsigned char* raw, int n, int K, int Gt) {
+  HalfSmem<real> s;
+  const int NR = 1 << K;
+  const int npairs = n * (n - 1) / 2;
+  real* p = reinterpret_cast<real*>(raw);
+  s.cp = p;
+  p += npairs * 8;
+  s.fcube = p;
+  p += n * NR * 2;
+  s.ecube = p;
+  p += NR;
+  s.fhi = p;
+  p += n * Gt * 2;
+  s.ehi = p;
+  p += Gt;
+  s.gz = p;
+  p += K * Gt;
+  size_t off = (reinterpret_cast<unsigned char*>(p) - raw + 15) & ~size_t(15);
+  s.red = reinterpret_cast<double*>(raw + off);
+  return s;
+}
+
+}  // namespace
+
+size_t half_smem_bytes(int n, int K, int rows_per_tile, int threads) {
+  const int NR = 1 << K, Gt = rows_per_tile >> K;
+  const size_t reals = (size_t)(n * (n - 1) / 2) * 8 + (size_t)n * NR * 2 + NR + (size_t)n * Gt * 2 + Gt + (size_t)K * Gt;
+  // sized for double tables; float tables use less
+  return ((reals * 8 + 15) & ~size_t(15)) + (size_t)threads * 4 * 8;
+}
+
+template <typename real, int K, int MODE>
+__global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ LaunchArgs a) {
+  constexpr int NR = 1 << K;
+  constexpr bool kPartials = MODE == kModeLanczos;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ InstDesc d;
+  __shared__ int is_last;
+  if (threadIdx.x == 0) d = a.inline_one ? a.one : a.inst[0];
+  __syncthreads();
+  const int n = d.n;
+  const int Gt = a.rows_per_tile >> K;
+  const HalfSmem<real> S = half_carve<real>(smem_raw, n, K, Gt);
+  const real* t = reinterpret_cast<const real*>(d.tab);
+  const TabLayout& L = d.lay;
+  const int bd = blockDim.x;
+  const int Rg = a.Rg;
+  const int kl = threadIdx.x % Rg;
+  const int slot = threadIdx.x / Rg, slots = bd / Rg;
+  const int R = a.R;
+
+  // ---- per-system tables ----
+  for (int q = threadIdx.x; q < n * n; q += bd) {
+    const int i = q / n, j = q % n;
+    if (i >= j) continue;
+    const int ij = i * n + j, p = tri(i, j);
+    const real pmr = t[L.off_pm + 2 * ij], pmi = t[L.off_pm + 2 * ij + 1];
+    const real ppr = t[L.off_pp + 2 * ij], ppi = t[L.off_pp + 2 * ij + 1];
+    real* c = S.cp + p * 8;
+    c[0] = ppr; c[1] = -ppi;   // (0,0): mu = s-_i s-_j nu
+    c[2] = pmr; c[3] = -pmi;   // (0,1): mu = s-_i s+_j nu
+    c[4] = pmr; c[5] = pmi;    // (1,0): mu = s+_i s-_j nu
+    c[6] = ppr; c[7] = ppi;    // (1,1): mu = s+_i s+_j nu
+  }
+  for (int q = threadIdx.x; q < n * NR; q += bd) {
+    const int j = q / NR, r = q % NR;
+    real fr = 0, fi = 0;
+    for (int c = 0; c < K; ++c) {
+      const real mc = ((r >> c) & 1) ? (real)0.5 : (real)-0.5;
+      fr += t[L.off_rho + 2 * (j * n + c)] * mc;
+      fi += t[L.off_rho + 2 * (j * n + c) + 1] * mc;
+    }
+    S.fcube[2 * q] = fr;
+    S.fcube[2 * q + 1] = fi;
+  }
+  for (int r = threadIdx.x; r < NR; r += bd) {
+    real e = 0;
+    for (int c = 0; c < K; ++c) {
+      const int bc = (r >> c) & 1;
+      const real mc = bc ? (real)0.5 : (real)-0.5;
+      e += t[L.off_hz + c] * mc + t[L.off_iondiag + c * L.qmax + bc];
+      for (int c2 = c + 1; c2 < K; ++c2) e += t[L.off_zz + c * n + c2] * mc * (((r >> c2) & 1) ? (real)0.5 : (real)-0.5);
+    }
+    S.ecube[r] = e;
+  }
+
+  double acc_d[4] = {0.0, 0.0, 0.0, 0.0};
+  if (kPartials) {
+    double* out = a.partials + (size_t)blockIdx.x * R * kNumPartials;
+    for (int k = threadIdx.x; k < R * kNumPartials; k += bd) out[k] = 0.0;
+  }
+  int cur_vg = -1;
+  real sig = 0, bsp = 0;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int vg = tile / a.tiles_per_vg;
+    const long long row0 = (long long)(tile - vg * a.tiles_per_vg) * a.rows_per_tile;
+    const int k = vg * Rg + kl;
+    const bool kvalid = k < R;
+    if (vg != cur_vg) {
+      if (kPartials && cur_vg >= 0) {  // flush the partials of the previous vector group
+        __syncthreads();
+        for (int c = 0; c < 4; ++c) S.red[threadIdx.x * 4 + c] = acc_d[c];
+        __syncthreads();
+        const int kk = cur_vg * Rg + threadIdx.x;
+        if ((int)threadIdx.x < Rg && kk < R) {
+          double sum[3] = {0, 0, 0};
+          for (int sl = 0; sl < slots; ++sl)
+            for (int c = 0; c < 3; ++c) sum[c] += S.red[(threadIdx.x + sl * Rg) * 4 + c];
+          double* out = a.partials + ((size_t)blockIdx.x * R + kk) * kNumPartials;
+          for (int c = 0; c < 3; ++c) out[c] = sum[c];
+        }
+        for (int c = 0; c < 4; ++c) acc_d[c] = 0.0;
+      }
+      if (kPartials && kvalid) {
+        sig = (real)d.sc.sigma[(size_t)a.step * R + k];
+        bsp = a.first ? (real)0 : (real)(d.sc.beta[(size_t)(a.step - 1) * R + k] * d.sc.sigma[(size_t)(a.step - 1) * R + k]);
+      }
+      cur_vg = vg;
+    }
+    __syncthreads();  // the previous tile's cubes are done with fhi / ehi / gz
+    // ---- per-tile outer parts ----
+    for (int q = threadIdx.x; q < n * Gt; q += bd) {
+      const int j = q / Gt, g = q % Gt;
+      const unsigned long long mu0 = (unsigned long long)(row0 + ((long long)g << K));
+      real fr = t[L.off_hp + 2 * j], fi = t[L.off_hp + 2 * j + 1];
+      for (int i = K; i < n; ++i) {
+        const real mi = ((mu0 >> i) & 1ull) ? (real)0.5 : (real)-0.5;
+        fr += t[L.off_rho + 2 * (j * n + i)] * mi;
+        fi += t[L.off_rho + 2 * (j * n + i) + 1] * mi;
+      }
+      S.fhi[2 * q] = fr;
+      S.fhi[2 * q + 1] = fi;
+    }
+    for (int g = threadIdx.x; g < Gt; g += bd) {
+      const unsigned long long mu0 = (unsigned long long)(row0 + ((long long)g << K));
+      real e = 0;
+      for (int i = K; i < n; ++i) {
+        const int bi = (mu0 >> i) & 1ull;
+        const real mi = bi ? (real)0.5 : (real)-0.5;
+        real zs = t[L.off_hz + i];
+        for (int j = i + 1; j < n; ++j) zs += t[L.off_zz + i * n + j] * (((mu0 >> j) & 1ull) ? (real)0.5 : (real)-0.5);
+        e += mi * zs + t[L.off_iondiag + i * L.qmax + bi];
+      }
+      S.ehi[g] = e;
+    }
+    for (int q = threadIdx.x; q < K * Gt; q += bd) {
+      const int c = q / Gt, g = q % Gt;
+      const unsigned long long mu0 = (unsigned long long)(row0 + ((long long)g << K));
+      real zs = 0;
+      for (int i = K; i < n; ++i) zs += t[L.off_zz + c * n + i] * (((mu0 >> i) & 1ull) ? (real)0.5 : (real)-0.5);
+      S.gz[q] = zs;
+    }
+    __syncthreads();
+    if (!kvalid) continue;
+    real pacc[3] = {0, 0, 0};
+    for (int g = slot; g < Gt; g += slots) {
+      const long long mu0 = row0 + ((long long)g << K);
+      if (mu0 >= d.dim) break;
+      const void* x = d.x;
+      real xr[NR], xi[NR], ar[NR], ai[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) VecIO<real, 1>::ldg(x, (mu0 + r) * R + k, &xr[r], &xi[r]);
+      // diagonal
+      {
+        const real eh = S.ehi[g];
+        real gzc[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) gzc[c] = S.gz[c * Gt + g];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          real e = eh + S.ecube[r];
+#pragma unroll
+          for (int c = 0; c < K; ++c) e += ((r >> c) & 1) ? (real)0.5 * gzc[c] : (real)-0.5 * gzc[c];
+          ar[r] = e * xr[r];
+          ai[r] = e * xi[r];
+        }
+      }
+      // flips of cube bits: single flips and pairs, all in registers
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const real fhr = S.fhi[2 * (c * Gt + g)], fhi_ = S.fhi[2 * (c * Gt + g) + 1];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const real fr = fhr + S.fcube[2 * (c * NR + r)];
+          const real fi = ((r >> c) & 1) ? fhi_ + S.fcube[2 * (c * NR + r) + 1] : -(fhi_ + S.fcube[2 * (c * NR + r) + 1]);
+          const int nb = r ^ (1 << c);
+          cmac<real, 1>(&ar[r], &ai[r], fr, fi, &xr[nb], &xi[nb]);
+        }
+#pragma unroll
+        for (int c1 = 0; c1 < c; ++c1) {
+          const real* cp = S.cp + tri(c1, c) * 8;
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const int idx = 2 * ((r >> c1) & 1) + ((r >> c) & 1);
+            const int nb = r ^ (1 << c) ^ (1 << c1);
+            cmac<real, 1>(&ar[r], &ai[r], cp[2 * idx], cp[2 * idx + 1], &xr[nb], &xi[nb]);
+          }
+        }
+      }
+      // outer bit j: the neighbouring cube serves the single flip of j and the mixed pairs (c, j)
+      for (int j = K; j < n; ++j) {
+        const int bj = (int)((mu0 >> j) & 1);
+        const long long nb0 = mu0 ^ (1ll << j);
+        real yr[NR], yi[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) VecIO<real, 1>::ldg(x, (nb0 + r) * R + k, &yr[r], &yi[r]);
+        const real fhr = S.fhi[2 * (j * Gt + g)], fhi_ = S.fhi[2 * (j * Gt + g) + 1];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const real fr = fhr + S.fcube[2 * (j * NR + r)];
+          const real fim = fhi_ + S.fcube[2 * (j * NR + r) + 1];
+          cmac<real, 1>(&ar[r], &ai[r], fr, bj ? fim : -fim, &yr[r], &yi[r]);
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          const real* cp = S.cp + tri(c, j) * 8;
+          const real c0r = cp[2 * bj], c0i = cp[2 * bj + 1];            // bit c of the row = 0
+          const real c1r = cp[2 * (2 + bj)], c1i = cp[2 * (2 + bj) + 1];  // bit c of the row = 1
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const int nb = r ^ (1 << c);
+            if ((r >> c) & 1) cmac<real, 1>(&ar[r], &ai[r], c1r, c1i, &yr[nb], &yi[nb]);
+            else cmac<real, 1>(&ar[r], &ai[r], c0r, c0i, &yr[nb], &yi[nb]);
+          }
+        }
+      }
+      // outer pairs (i, j): one coefficient for the whole cube
+      for (int j = K + 1; j < n; ++j) {
+        const int bj = (int)((mu0 >> j) & 1);
+        const real* cpj = S.cp + tri(K, j) * 8 + 2 * bj;
+        for (int i = K; i < j; ++i) {
+          const int bi = (int)((mu0 >> i) & 1);
+          const real* cp = cpj + (i - K) * 8 + 4 * bi;
+          const real cr = cp[0], ci = cp[1];
+          const long long nb0 = mu0 ^ (1ll << j) ^ (1ll << i);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            real yr, yi;
+            VecIO<real, 1>::ldg(x, (nb0 + r) * R + k, &yr, &yi);
+            cmac<real, 1>(&ar[r], &ai[r], cr, ci, &yr, &yi);
+          }
+        }
+      }
+      // epilogue
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const long long idx = (mu0 + r) * R + k;
+        if (MODE == kModeApply) {
+          VecIO<real, 1>::st(d.y, idx, &ar[r], &ai[r]);
+        } else {
+          real wr = sig * ar[r], wi = sig * ai[r];
+          if (!a.first) {
+            real qr, qi;
+            VecIO<real, 1>::ld(d.y, idx, &qr, &qi);
+            wr = fma(-bsp, qr, wr);
+            wi = fma(-bsp, qi, wi);
+          }
+          VecIO<real, 1>::st(d.y, idx, &wr, &wi);
+          real ur, ui;
+          VecIO<real, 1>::ldg(d.u, idx, &ur, &ui);
+          const real vr = sig * xr[r], vi = sig * xi[r];
+          pacc[0] += vr * wr + vi * wi;
+          pacc[1] += vr * ur + vi * ui;
+          pacc[2] += vr * ui - vi * ur;
+        }
+      }
+    }
+    if (kPartials)
+      for (int c = 0; c < 3; ++c) acc_d[c] += (double)pacc[c];
+  }
+  if (!kPartials) return;
+  if (cur_vg >= 0) {
+    __syncthreads();
+    for (int c = 0; c < 4; ++c) S.red[threadIdx.x * 4 + c] = acc_d[c];
+    __syncthreads();
+    const int kk = cur_vg * Rg + threadIdx.x;
+    if ((int)threadIdx.x < Rg && kk < R) {
+      double sum[3] = {0, 0, 0};
+      for (int sl = 0; sl < slots; ++sl)
+        for (int c = 0; c < 3; ++c) sum[c] += S.red[(threadIdx.x + sl * Rg) * 4 + c];
+      double* out = a.partials + ((size_t)blockIdx.x * R + kk) * kNumPartials;
+      for (int c = 0; c < 3; ++c) out[c] = sum[c];
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  finalize(a, a.inline_one ? &a.one : a.inst);
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+template <typename real, int K>
+static int launch_k(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (a.mode == kModeApply) half_kernel<real, K, kModeApply><<<grid, threads, smem, st>>>(a);
+  else if (a.mode == kModeLanczos) half_kernel<real, K, kModeLanczos><<<grid, threads, smem, st>>>(a);
+  else return (int)cudaErrorInvalidValue;
+  return (int)cudaGetLastError();
+}
+
+int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size_t smem, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (c64) {
+    switch (K) {
+      case 2: return launch_k<float, 2>(a, grid, threads, smem, st);
+      case 3: return launch_k<float, 3>(a, grid, threads, smem, st);
+      case 4: return launch_k<float, 4>(a, grid, threads, smem, st);
+    }
+  } else {
+    switch (K) {
+      case 2: return launch_k<double, 2>(a, grid, threads, smem, st);
+      case 3: return launch_k<double, 3>(a, grid, threads, smem, st);
+      case 4: return launch_k<double, 4>(a, grid, threads, smem, st);
+    }
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <typename real, int K>
+static int allow_half(int bytes) {
+  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply>, (const void*)half_kernel<real, K, kModeLanczos>};
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
+}
+
+int prepare_half_kernels(size_t smem) {
+  int e = allow_half<float, 2>((int)smem);
+  if (!e) e = allow_half<float, 3>((int)smem);
+  if (!e) e = allow_half<float, 4>((int)smem);
+  if (!e) e = allow_half<double, 2>((int)smem);
+  if (!e) e = allow_half<double, 3>((int)smem);
+  if (!e) e = allow_half<double, 4>((int)smem);
+  return e;
+}
+
+int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (c64) {
+    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 2, kModeLanczos>, threads, smem);
+    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 3, kModeLanczos>, threads, smem);
+    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 4, kModeLanczos>, threads, smem);
+  } else {
+    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 2, kModeLanczos>, threads, smem);
+    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 3, kModeLanczos>, threads, smem);
+    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 4, kModeLanczos>, threads, smem);
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+}  // namespace ftlm

@@ -1,0 +1,563 @@
+// CUDA kernels of the FTLM hot path (arxiv 2607.25585, Secs. II.A-II.C):
+//  * the matrix-free row-gather H.v over the (2s+1)^N product basis, with
+//    the coupling tables of Eq. (3) staged in shared memory and every matrix
+//    element evaluated on the fly (no stored matrix, no atomics);
+//  * the Lanczos step epilogue fused into the matvec (w = H v_j - beta_j
+//    v_{j-1}, in place over v_{j-1}, with the partial sums of
+//    alpha_j = Re<v_j|w> and p_j = <v_j|u>), the orthogonalisation update,
+//    the start-vector norm and the observable u.S;
+//  * deterministic two-stage reductions: per-CTA partials in FP64, then the
+//    last CTA to finish sums them in a fixed order and writes the Lanczos
+//    scalars (alpha, p, beta, the breakdown test and the vector scales).
+//
+// Vector blocks are [dim][R] complex, R fastest.  A thread owns one row and
+// a chunk of V consecutive vectors (16 bytes: V = 2 for complex64, 1 for
+// complex128), so a warp reads whole 512-byte rows when R = 64.
+// Lanczos vectors are kept unnormalised: v_j = sigma_j q_j, with sigma_j in
+// device memory, which saves a normalisation pass per step.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "ftlm_internal.h"
+
+namespace ftlm {
+
+// ---------------------------------------------------------------------------
+// shared-memory staging of one instance's tables
+// ---------------------------------------------------------------------------
+struct SmemView {
+  void* tab;
+  long long* stride;
+  int* q;
+  unsigned char* dig;   // [max_n][blockDim]
+  double* red;          // [blockDim][kNumPartials * V]
+};
+
+template <typename real>
+__device__ SmemView carve(unsigned char* raw, const LaunchArgs& a, int V) {
+  SmemView s;
+  size_t off = 0;
+  s.tab = raw;
+  off += ((size_t)a.tab_reals * sizeof(real) + 15) & ~size_t(15);
+  s.stride = reinterpret_cast<long long*>(raw + off);
+  off += (size_t)a.max_n * 8;
+  s.q = reinterpret_cast<int*>(raw + off);
+  off += ((size_t)a.max_n * 4 + 15) & ~size_t(15);
+  s.red = reinterpret_cast<double*>(raw + off);
+  off += (size_t)blockDim.x * kNumPartials * V * 8;
+  s.dig = raw + off;
+  return s;
+}
+
+template <typename real>
+__device__ void stage_instance(const InstDesc& d, const SmemView& s) {
+  const real* src = reinterpret_cast<const real*>(d.tab);
+  real* dst = reinterpret_cast<real*>(s.tab);
+  for (int i = threadIdx.x; i < d.lay.total; i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x; i < d.n; i += blockDim.x) {
+    s.stride[i] = d.stride[i];
+    s.q[i] = d.q[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one row of H x (Eq. 3), general mixed radix.  Row mu gathers from every
+// nu with <mu|H|nu> != 0: the diagonal, single-site +-1 and +-2 steps, and
+// the four +-1/+-1 pair steps of every pair i < j.
+// ---------------------------------------------------------------------------
+template <typename real, int V>
+__device__ __forceinline__ void h_row(const SmemView& s, const TabLayout& L, int n, long long mu, bool idx32,
+                                      const void* __restrict__ x, int R, int col, real* ar, real* ai, real* xr_own,
+                                      real* xi_own) {
+  const real* t = reinterpret_cast<const real*>(s.tab);
+  const int qm = L.qmax;
+  unsigned char* dg = s.dig + threadIdx.x;
+  const int bd = blockDim.x;
+  // mixed-radix digits of mu, site 0 least significant
+  if (idx32) {
+    unsigned rem = (unsigned)mu;
+    for (int i = 0; i < n; ++i) {
+      const unsigned qi = (unsigned)s.q[i];
+      const unsigned nq = rem / qi;
+      dg[i * bd] = (unsigned char)(rem - nq * qi);
+      rem = nq;
+    }
+  } else {
+    unsigned long long rem = (unsigned long long)mu;
+    for (int i = 0; i < n; ++i) {
+      const unsigned long long qi = (unsigned long long)s.q[i];
+      const unsigned long long nq = rem / qi;
+      dg[i * bd] = (unsigned char)(rem - nq * qi);
+      rem = nq;
+    }
+  }
+  // diagonal: sum_{i<j} zz m_i m_j + sum_i (h_z m_i + single-ion diagonal)
+  real diag = 0;
+  for (int i = 0; i < n; ++i) {
+    const int ai_ = dg[i * bd];
+    const real mi = t[L.off_m + i * qm + ai_];
+    real zsum = t[L.off_hz + i];
+    for (int j = i + 1; j < n; ++j) zsum = fma(t[L.off_zz + i * n + j], t[L.off_m + j * qm + dg[j * bd]], zsum);
+    diag = fma(mi, zsum, diag);
+    diag += t[L.off_iondiag + i * qm + ai_];
+  }
+  VecIO<real, V>::ldg(x, mu * R + col, xr_own, xi_own);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    ar[v] = diag * xr_own[v];
+    ai[v] = diag * xi_own[v];
+  }
+  for (int i = 0; i < n; ++i) {
+    const int a_i = dg[i * bd];
+    const int qi = s.q[i];
+    const long long si = s.stride[i];
+    const real mi = t[L.off_m + i * qm + a_i];
+    const real up_i = t[L.off_up1 + i * qm + a_i];
+    const real dn_i = t[L.off_dn1 + i * qm + a_i];
+    // coefficient of the s+_i-type single steps: h+_i + sum_j rho_ij m_j
+    real fr = t[L.off_hp + 2 * i], fi = t[L.off_hp + 2 * i + 1];
+    for (int j = 0; j < n; ++j) {
+      const real mj = t[L.off_m + j * qm + dg[j * bd]];
+      fr = fma(t[L.off_rho + 2 * (i * n + j)], mj, fr);
+      fi = fma(t[L.off_rho + 2 * (i * n + j) + 1], mj, fi);
+    }
+    const real bzr = t[L.off_bz + 2 * i], bzi = t[L.off_bz + 2 * i + 1];
+    if (a_i >= 1) {  // mu = s+_i nu: (F + bz (2m - 1)) <a|s+|a-1>
+      const real w = (real)2 * mi - (real)1;
+      gather_mac<real, V>(x, mu - si, R, col, (fr + bzr * w) * up_i, (fi + bzi * w) * up_i, ar, ai);
+    }
+    if (a_i + 1 < qi) {  // mu = s-_i nu: conj(F + bz (2m + 1)) <a|s-|a+1>
+      const real w = (real)2 * mi + (real)1;
+      gather_mac<real, V>(x, mu + si, R, col, (fr + bzr * w) * dn_i, -(fi + bzi * w) * dn_i, ar, ai);
+    }
+    if (a_i >= 2) {
+      const real u2 = t[L.off_up2 + i * qm + a_i];
+      gather_mac<real, V>(x, mu - 2 * si, R, col, t[L.off_bb + 2 * i] * u2, t[L.off_bb + 2 * i + 1] * u2, ar, ai);
+    }
+    if (a_i + 2 < qi) {
+      const real d2 = t[L.off_dn2 + i * qm + a_i];
+      gather_mac<real, V>(x, mu + 2 * si, R, col, t[L.off_bb + 2 * i] * d2, -t[L.off_bb + 2 * i + 1] * d2, ar, ai);
+    }
+    for (int j = i + 1; j < n; ++j) {
+      const int a_j = dg[j * bd];
+      const int qj = s.q[j];
+      const long long sj = s.stride[j];
+      const real up_j = t[L.off_up1 + j * qm + a_j];
+      const real dn_j = t[L.off_dn1 + j * qm + a_j];
+      const int ij = i * n + j;
+      const real pmr = t[L.off_pm + 2 * ij], pmi = t[L.off_pm + 2 * ij + 1];
+      const real ppr = t[L.off_pp + 2 * ij], ppi = t[L.off_pp + 2 * ij + 1];
+      const bool iu = a_i >= 1, id = a_i + 1 < qi, ju = a_j >= 1, jd = a_j + 1 < qj;
+      if (iu && jd) {  // mu = s+_i s-_j nu
+        const real e = up_i * dn_j;
+        gather_mac<real, V>(x, mu - si + sj, R, col, pmr * e, pmi * e, ar, ai);
+      }
+      if (id && ju) {  // mu = s-_i s+_j nu
+        const real e = dn_i * up_j;
+        gather_mac<real, V>(x, mu + si - sj, R, col, pmr * e, -pmi * e, ar, ai);
+      }
+      if (iu && ju) {  // mu = s+_i s+_j nu
+        const real e = up_i * up_j;
+        gather_mac<real, V>(x, mu - si - sj, R, col, ppr * e, ppi * e, ar, ai);
+      }
+      if (id && jd) {  // mu = s-_i s-_j nu
+        const real e = dn_i * dn_j;
+        gather_mac<real, V>(x, mu + si + sj, R, col, ppr * e, -ppi * e, ar, ai);
+      }
+    }
+  }
+}
+
+// one row of (u.S) x: u_z sum_i m_i x_mu + a_u <a|s+|a-1> x_{mu - s_i} + conj(a_u) <a|s-|a+1> x_{mu + s_i}
+template <typename real, int V>
+__device__ __forceinline__ void s_row(const SmemView& s, const TabLayout& L, int n, long long mu, bool idx32,
+                                      const void* __restrict__ x, int R, int col, real uz, real aur, real aui,
+                                      real* ar, real* ai) {
+  const real* t = reinterpret_cast<const real*>(s.tab);
+  const int qm = L.qmax;
+  real msum = 0;
+#pragma unroll
+  for (int v = 0; v < V; ++v) ar[v] = ai[v] = 0;
+  unsigned long long rem = (unsigned long long)mu;
+  unsigned rem32 = (unsigned)mu;
+  for (int i = 0; i < n; ++i) {
+    int a_i;
+    if (idx32) {
+      const unsigned nq = rem32 / (unsigned)s.q[i];
+      a_i = (int)(rem32 - nq * (unsigned)s.q[i]);
+      rem32 = nq;
+    } else {
+      const unsigned long long nq = rem / (unsigned long long)s.q[i];
+      a_i = (int)(rem - nq * (unsigned long long)s.q[i]);
+      rem = nq;
+    }
+    msum += t[L.off_m + i * qm + a_i];
+    if (a_i >= 1) {
+      const real e = t[L.off_up1 + i * qm + a_i];
+      gather_mac<real, V>(x, mu - s.stride[i], R, col, aur * e, aui * e, ar, ai);
+    }
+    if (a_i + 1 < s.q[i]) {
+      const real e = t[L.off_dn1 + i * qm + a_i];
+      gather_mac<real, V>(x, mu + s.stride[i], R, col, aur * e, -aui * e, ar, ai);
+    }
+  }
+  real xr[V], xi[V];
+  VecIO<real, V>::ldg(x, mu * R + col, xr, xi);
+  const real dz = uz * msum;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    ar[v] = fma(dz, xr[v], ar[v]);
+    ai[v] = fma(dz, xi[v], ai[v]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order reductions
+// ---------------------------------------------------------------------------
+// Sums thread accumulators acc[V*kNumPartials] over the threads of the CTA
+// that own the same vector chunk (tid % C) and writes the CTA's partials for
+// instance `inst`.  All threads must call it.
+template <int V>
+__device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst, double* acc) {
+  const int np = V * kNumPartials;
+  __syncthreads();
+  for (int k = 0; k < np; ++k) s.red[threadIdx.x * np + k] = acc[k];
+  __syncthreads();
+  const int C = a.C;
+  const int per = blockDim.x / C;
+  if ((int)threadIdx.x < C) {
+    double sum[V * kNumPartials];
+    for (int k = 0; k < np; ++k) sum[k] = 0.0;
+    for (int r = 0; r < per; ++r)
+      for (int k = 0; k < np; ++k) sum[k] += s.red[(threadIdx.x + r * C) * np + k];
+    double* out = a.partials + ((size_t)inst * gridDim.x + blockIdx.x) * (size_t)a.R * kNumPartials;
+    for (int v = 0; v < V; ++v)
+      for (int c = 0; c < kNumPartials; ++c) out[(threadIdx.x * V + v) * kNumPartials + c] = sum[v * kNumPartials + c];
+  }
+  __syncthreads();
+  for (int k = 0; k < np; ++k) acc[k] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// the tile loop shared by every mode
+// ---------------------------------------------------------------------------
+template <typename real, int V, int MODE>
+__global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ LaunchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SmemView s = carve<real>(smem_raw, a, V);
+  __shared__ InstDesc d;
+  __shared__ int is_last;
+  constexpr bool kPartials = MODE == kModeLanczos || MODE == kModeUpdate || MODE == kModeStartNorm;
+  const InstDesc* insts = a.inline_one ? &a.one : a.inst;
+  constexpr int NP = V * kNumPartials;
+  double acc[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) acc[k] = 0.0;
+
+  const int C = a.C;
+  const int chunk = threadIdx.x % C;   // fixed per thread: blockDim is a multiple of C
+  const int col = chunk * V;
+
+  if (kPartials) {  // zero this CTA's slots of every instance
+    for (int inst = 0; inst < a.n_inst; ++inst) {
+      double* out = a.partials + ((size_t)inst * gridDim.x + blockIdx.x) * (size_t)a.R * kNumPartials;
+      for (int k = threadIdx.x; k < a.R * kNumPartials; k += blockDim.x) out[k] = 0.0;
+    }
+  }
+  int cur = -1;
+  real sig[V], bsp[V], coef[V];  // per-vector scalars of the current instance
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int inst = a.inline_one ? 0 : find_instance(a.tile_start, a.n_inst, tile);
+    if (inst != cur) {
+      if (kPartials && cur >= 0) flush_partials<V>(a, s, cur, acc);
+      __syncthreads();
+      if (threadIdx.x == 0) d = insts[inst];
+      __syncthreads();
+      if (MODE == kModeApply || MODE == kModeLanczos || MODE == kModeApplyS) stage_instance<real>(d, s);
+      const int j = a.step;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int k = min(col + v, a.R - 1);
+        sig[v] = bsp[v] = coef[v] = 0;
+        if (MODE == kModeLanczos) {
+          sig[v] = (real)d.sc.sigma[(size_t)j * a.R + k];
+          if (!a.first) bsp[v] = (real)(d.sc.beta[(size_t)(j - 1) * a.R + k] * d.sc.sigma[(size_t)(j - 1) * a.R + k]);
+        } else if (MODE == kModeUpdate) {
+          coef[v] = (real)(d.sc.alpha[(size_t)j * a.R + k] * d.sc.sigma[(size_t)j * a.R + k]);
+        } else if (MODE == kModeApplyS) {
+          coef[v] = a.use_sigma0 ? (real)d.sc.sigma[k] : (real)1;
+        } else if (MODE == kModeScale) {
+          coef[v] = (real)d.sc.sigma[k];
+        }
+      }
+      cur = inst;
+      __syncthreads();
+    }
+    const int first_tile = a.inline_one ? 0 : __ldg(a.tile_start + inst);
+    const long long row0 = (long long)(tile - first_tile) * a.rows_per_tile;
+    const bool idx32 = d.dim <= 0xffffffffll;
+    real pacc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pacc[k] = 0;
+    const int items = a.rows_per_tile * C;
+    for (int item = threadIdx.x; item < items; item += blockDim.x) {
+      const long long row = row0 + item / C;
+      if (row >= d.dim) break;
+      const long long idx = row * a.R + col;
+      if (MODE == kModeApply || MODE == kModeLanczos) {
+        real ar[V], ai[V], xr[V], xi[V];
+        h_row<real, V>(s, d.lay, d.n, row, idx32, d.x, a.R, col, ar, ai, xr, xi);
+        if (MODE == kModeApply) {
+          VecIO<real, V>::st(d.y, idx, ar, ai);
+        } else {
+          real wr[V], wi[V];
+          if (!a.first) {
+            real qr[V], qi[V];
+            VecIO<real, V>::ld(d.y, idx, qr, qi);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              wr[v] = fma(sig[v], ar[v], -bsp[v] * qr[v]);
+              wi[v] = fma(sig[v], ai[v], -bsp[v] * qi[v]);
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              wr[v] = sig[v] * ar[v];
+              wi[v] = sig[v] * ai[v];
+            }
+          }
+          VecIO<real, V>::st(d.y, idx, wr, wi);
+          real ur[V], ui[V];
+          VecIO<real, V>::ldg(d.u, idx, ur, ui);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
+            pacc[v * kNumPartials + 0] += vr * wr[v] + vi * wi[v];     // Re <v|w>
+            pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];     // Re <v|u>
+            pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];     // Im <v|u>
+          }
+        }
+      } else if (MODE == kModeUpdate) {
+        real wr[V], wi[V], xr[V], xi[V];
+        VecIO<real, V>::ld(d.y, idx, wr, wi);
+        VecIO<real, V>::ldg(d.x, idx, xr, xi);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          wr[v] = fma(-coef[v], xr[v], wr[v]);
+          wi[v] = fma(-coef[v], xi[v], wi[v]);
+          pacc[v * kNumPartials] += wr[v] * wr[v] + wi[v] * wi[v];
+        }
+        VecIO<real, V>::st(d.y, idx, wr, wi);
+      } else if (MODE == kModeStartNorm) {
+        real xr[V], xi[V];
+        VecIO<real, V>::ldg(d.x, idx, xr, xi);
+#pragma unroll
+        for (int v = 0; v < V; ++v) pacc[v * kNumPartials] += xr[v] * xr[v] + xi[v] * xi[v];
+      } else if (MODE == kModeScale) {
+        real xr[V], xi[V];
+        VecIO<real, V>::ld(d.x, idx, xr, xi);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          xr[v] *= coef[v];
+          xi[v] *= coef[v];
+        }
+        VecIO<real, V>::st(d.y, idx, xr, xi);
+      } else if (MODE == kModeApplyS) {
+        real ar[V], ai[V];
+        s_row<real, V>(s, d.lay, d.n, row, idx32, d.x, a.R, col, (real)d.obs[0], (real)d.obs[1], (real)d.obs[2],
+                       ar, ai);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          ar[v] *= coef[v];
+          ai[v] *= coef[v];
+        }
+        VecIO<real, V>::st(d.y, idx, ar, ai);
+      }
+    }
+    if (kPartials) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) acc[k] += (double)pacc[k];
+    }
+  }
+  if (!kPartials) return;
+  if (cur >= 0) flush_partials<V>(a, s, cur, acc);
+  // last CTA to arrive reduces every CTA's partials in a fixed order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  finalize(a, insts);
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// start vectors: Philox4x32-10 (Salmon et al., SC'11), Box-Muller in FP64
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox_round(unsigned& c0, unsigned& c1, unsigned& c2, unsigned& c3, unsigned k0,
+                                             unsigned k1) {
+  const unsigned lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+  const unsigned lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+  const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+  c0 = n0;
+  c1 = lo1;
+  c2 = n2;
+  c3 = lo0;
+}
+
+__device__ __forceinline__ void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c[0], c[1], c[2], c[3], k0, k1);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ double unit53(unsigned hi, unsigned lo) {
+  const unsigned long long k = ((unsigned long long)hi << 21) | ((unsigned long long)lo >> 11);
+  return ((double)k + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+template <typename real>
+__global__ void start_random_kernel(long long dim, int R, unsigned long long seed, unsigned long long vec_offset,
+                                    real* out) {
+  const long long total = dim * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long nu = e / R;
+    const unsigned long long rg = vec_offset + (unsigned long long)(e - nu * R);
+    unsigned c[4] = {(unsigned)nu, (unsigned)((unsigned long long)nu >> 32), (unsigned)rg, (unsigned)(rg >> 32)};
+    philox4x32_10(c, (unsigned)seed, (unsigned)(seed >> 32));
+    const double u1 = unit53(c[0], c[1]);
+    const double u2 = unit53(c[2], c[3]);
+    const double rho = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[2 * e] = (real)(rho * cs);
+    out[2 * e + 1] = (real)(rho * sn);
+  }
+}
+
+template <typename real>
+__global__ void start_basis_kernel(long long dim, int R, unsigned long long basis_offset, real* out) {
+  const long long total = dim * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long nu = e / R;
+    const long long k = e - nu * R;
+    out[2 * e] = (real)((unsigned long long)nu == basis_offset + (unsigned long long)k ? 1.0 : 0.0);
+    out[2 * e + 1] = (real)0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads) {
+  const int V = c64 ? 2 : 1;
+  const size_t realsz = c64 ? 4 : 8;
+  size_t off = ((size_t)a.tab_reals * realsz + 15) & ~size_t(15);
+  off += (size_t)a.max_n * 8;
+  off += ((size_t)a.max_n * 4 + 15) & ~size_t(15);
+  off += (size_t)threads * kNumPartials * V * 8;
+  off += (size_t)a.max_n * threads;
+  return off;
+}
+
+template <typename real, int V, int MODE>
+static int launch_one(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  rows_kernel<real, V, MODE><<<grid, threads, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <typename real, int V>
+static int allow_smem(int bytes) {
+  const void* ks[] = {(const void*)rows_kernel<real, V, kModeApply>, (const void*)rows_kernel<real, V, kModeLanczos>,
+                      (const void*)rows_kernel<real, V, kModeUpdate>, (const void*)rows_kernel<real, V, kModeStartNorm>,
+                      (const void*)rows_kernel<real, V, kModeApplyS>, (const void*)rows_kernel<real, V, kModeScale>};
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
+}
+
+// Raises the dynamic shared-memory limit of every row kernel; called outside
+// stream capture before the first launch that needs more than 48 KB.
+int prepare_rows_kernels(size_t smem) {
+  int e = allow_smem<float, 2>((int)smem);
+  if (!e) e = allow_smem<float, 1>((int)smem);
+  if (!e) e = allow_smem<double, 1>((int)smem);
+  return e;
+}
+
+template <typename real, int V>
+static int launch_mode(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  switch (a.mode) {
+    case kModeApply: return launch_one<real, V, kModeApply>(a, grid, threads, smem, st);
+    case kModeLanczos: return launch_one<real, V, kModeLanczos>(a, grid, threads, smem, st);
+    case kModeUpdate: return launch_one<real, V, kModeUpdate>(a, grid, threads, smem, st);
+    case kModeStartNorm: return launch_one<real, V, kModeStartNorm>(a, grid, threads, smem, st);
+    case kModeApplyS: return launch_one<real, V, kModeApplyS>(a, grid, threads, smem, st);
+    case kModeScale: return launch_one<real, V, kModeScale>(a, grid, threads, smem, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+int launch_rows(const LaunchArgs& a, int c64, int grid, int threads, size_t smem, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (c64) {
+    if (a.R % 2 == 0) return launch_mode<float, 2>(a, grid, threads, smem, st);
+    return launch_mode<float, 1>(a, grid, threads, smem, st);
+  }
+  return launch_mode<double, 1>(a, grid, threads, smem, st);
+}
+
+int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int mode) {
+  int n = 0;
+  cudaError_t e;
+  (void)mode;  // the caller has raised the shared-memory limit to >= smem
+  if (c64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<float, 2, kModeLanczos>, threads, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<double, 1, kModeLanczos>, threads, smem);
+  return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+int launch_start_random(const InstDesc* inst_host, const InstDesc*, int R, uint64_t seed, uint64_t vec_offset,
+                        void* out, int c64, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long total = inst_host->dim * R;
+  const int threads = 256;
+  const long long want = (total + threads - 1) / threads;
+  const int grid = (int)(want < 152LL * 16 ? want : 152LL * 16);
+  if (c64) start_random_kernel<float><<<grid, threads, 0, st>>>(inst_host->dim, R, seed, vec_offset, (float*)out);
+  else start_random_kernel<double><<<grid, threads, 0, st>>>(inst_host->dim, R, seed, vec_offset, (double*)out);
+  return (int)cudaGetLastError();
+}
+
+int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long total = dim * R;
+  const int threads = 256;
+  const long long want = (total + threads - 1) / threads;
+  const int grid = (int)(want < 152LL * 16 ? want : 152LL * 16);
+  if (c64) start_basis_kernel<float><<<grid, threads, 0, st>>>(dim, R, basis_offset, (float*)out);
+  else start_basis_kernel<double><<<grid, threads, 0, st>>>(dim, R, basis_offset, (double*)out);
+  return (int)cudaGetLastError();
+}
+
+int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream) {
+  return (int)cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+}  // namespace ftlm

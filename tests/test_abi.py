@@ -1,0 +1,73 @@
+"""The C-ABI library loads, exports every symbol include/ftlm.h declares, and
+its host-only parts work without a GPU (argument validation happens before
+any CUDA call; ftlm_sums is pure host code)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import ftlm_workloads as W
+import oracle
+import paper_2607_25585_gb300 as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    F.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ftlm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ftlm_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 10
+    L = F.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(F.EXPORTS) == names
+
+
+def test_version():
+    assert "sm_103a" in F.version()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(two_s=[1, 0]), "two_s"),
+    (dict(two_s=[1, 16]), "two_s"),
+    (dict(two_s=[1, 1], pos=np.zeros((2, 3))), "coincide"),
+    (dict(two_s=[2, 2], d_ion=[1.0, 0.0], e_axes=np.zeros((2, 3))), "e_axes"),
+    (dict(two_s=[1, 1], B=[0.0, np.nan, 0.0]), "finite"),
+    (dict(two_s=[1] * 37), "2^36"),
+])
+def test_invalid_systems_rejected_on_host(kw, msg):
+    with pytest.raises(F.FtlmError) as e:
+        F.System(**kw)
+    assert msg in str(e.value)
+
+
+def test_sums_match_oracle(rng):
+    """ftlm_sums (implicit QL on the host) against the oracle's sums (cyclic
+    Jacobi) on the same tridiagonal data."""
+    s = oracle.System(**{k: v for k, v in W.ring(N=4, two_s=2).items() if k != "name"})
+    T = W.temperatures()
+    o = oracle.ftlm(s, R=4, M=30, T=T, seed=3)
+    r = F.sums(o["alpha"], o["beta"], o["p"], o["M_eff"], s.dim, s.g, T)
+    for k in ("lnZ", "E", "C", "M_B", "M_B_imag"):
+        ref = o[k]
+        scale = np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max() + 1e-300)
+        assert np.max(np.abs(r[k] - ref) / scale) < 1e-10, k
+    assert abs(r["E0"] - o["E0"]) < 1e-12 * abs(o["E0"])
+
+
+def test_sums_reject_bad_input():
+    with pytest.raises(F.FtlmError):
+        F.sums(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)), [4], 8, 2.0, [1.0])
+    with pytest.raises(F.FtlmError):
+        F.sums(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)), [2], 8, 2.0, [0.0])
