@@ -294,6 +294,37 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_hv_only(args):
+    """The dominant kernel alone: args.hv_only launches of H.v on the bench
+    workload's [d][R] complex64 block (the same kernel and launch shape the
+    Lanczos steps use), timed with CUDA events.  Used for ncu captures."""
+    import torch
+
+    import paper_2607_25585_gb300 as F
+
+    F.build()
+    spec = W.WORKLOADS[WORKLOAD]
+    w = spec["system"]()
+    s = F.System.from_dict(w)
+    d, R = s.dim, spec["R"]
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(d, R, dtype=torch.complex64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    for _ in range(2):
+        F.apply_h(s, x, y, R, "c64")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.hv_only):
+        F.apply_h(s, x, y, R, "c64")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.hv_only
+    return {"mode": "hv_only", "workload": WORKLOAD, "d": d, "R": R, "launches": args.hv_only,
+            "ms_per_launch": ms, "states_vectors_per_s": d * R / (ms / 1e3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,7 +337,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--hv-only", type=int, default=0, help="time N launches of the H.v kernel alone")
     args = ap.parse_args()
+    if args.hv_only:
+        print(json.dumps(run_hv_only(args)), flush=True)
+        return
     if args.warmup < 3:
         args.warmup = 3
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -146,6 +146,7 @@ InstDesc base_desc(const ftlm_system* s, int c64) {
 
 struct HalfPlan {
   bool on = false;
+  int real_pm = 0;
   int K = 3, Rg = 1, threads = 256, rows_per_tile = 0, grid = 0, nvg = 0, tiles_per_vg = 0;
   size_t smem = 0;
 };
@@ -174,6 +175,7 @@ bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_fac
   h = HalfPlan();
   h.K = K;
   h.Rg = Rg;
+  h.real_pm = hs.real_pm ? 1 : 0;
   const int slots = std::max(1, 256 / Rg);
   h.threads = slots * Rg;
   long long rows = (long long)slots * (1ll << K) * rows_factor;
@@ -181,7 +183,7 @@ bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_fac
   rows = std::max<long long>(rows, 1ll << K);
   h.rows_per_tile = (int)rows;
   h.nvg = (R + Rg - 1) / Rg;
-  h.tiles_per_vg = (int)((long long)hs.dim / rows);
+  h.tiles_per_vg = (int)(((long long)hs.dim + rows - 1) / rows);  // the last tile may be ragged
   const long long ntiles = (long long)h.tiles_per_vg * h.nvg;
   if (ntiles > (1ll << 30)) return false;
   h.smem = half_smem_bytes(hs.n, K, h.rows_per_tile, h.threads);
@@ -238,7 +240,7 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   if (sys.size() == 1 && pl.sh.half_K > 0)
     make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.half);
   else if (sys.size() == 1 && !force && !pl.sh.explicit_general && sys[0]->hs.all_half)
-    make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 16), 2, pl.half);
+    make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 64), 2, pl.half);
   return FTLM_OK;
 }
 
@@ -251,6 +253,7 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.nvg = pl.half.nvg;
     a.tiles_per_vg = pl.half.tiles_per_vg;
     a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
+    a.real_pm = pl.half.real_pm;
     return launch_half(a, pl.half.K, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
   }
   return launch_rows(a, pl.c64, pl.grid, pl.sh.threads, pl.smem, st);
@@ -601,7 +604,7 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
   std::vector<Shape> cands;
   if (s->hs.all_half && s->hs.n >= 4) {
     std::vector<int> rgs;
-    for (int cap : {16, 8, 4}) {
+    for (int cap : {64, 32, 16}) {
       const int g = largest_divisor_at_most(R, cap);
       if (std::find(rgs.begin(), rgs.end(), g) == rgs.end()) rgs.push_back(g);
     }

@@ -126,6 +126,7 @@ struct LaunchArgs {
   int Rg = 0;           // vectors per group
   int nvg = 0;          // number of vector groups = ceil(R / Rg)
   int tiles_per_vg = 0; // row tiles per vector group
+  int real_pm = 0;      // every s+ s- coefficient is real (symmetric coupling tensors)
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.

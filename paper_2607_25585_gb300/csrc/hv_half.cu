@@ -74,8 +74,61 @@ size_t half_smem_bytes(int n, int K, int rows_per_tile, int threads) {
   return ((reals * 8 + 15) & ~size_t(15)) + (size_t)threads * 4 * 8;
 }
 
-template <typename real, int K, int MODE>
+// Complex accumulators.  FP32: two packed accumulators updated with the
+// Blackwell f32x2 FMA, a = sum c_re x and b = sum c_im x (x = (re, im)), so a
+// complex multiply-add is two FFMA2 and a real one (the s+ s- coefficients of
+// a symmetric coupling tensor) is one; the value is (a.x - b.y, a.y + b.x).
+// FP64: plain FMAs.
+template <typename real>
+struct Cx;
+
+template <>
+struct Cx<float> {
+  using v2 = float2;
+  float2 a, b;
+  __device__ __forceinline__ void set(float e, float2 x) {
+    a = make_float2(e * x.x, e * x.y);
+    b = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void mac(float cr, float ci, float2 x) {
+    a = __ffma2_rn(make_float2(cr, cr), x, a);
+    b = __ffma2_rn(make_float2(ci, ci), x, b);
+  }
+  __device__ __forceinline__ void mac_re(float cr, float2 x) { a = __ffma2_rn(make_float2(cr, cr), x, a); }
+  __device__ __forceinline__ float2 value() const { return make_float2(a.x - b.y, a.y + b.x); }
+};
+
+template <>
+struct Cx<double> {
+  using v2 = double2;
+  double re, im;
+  __device__ __forceinline__ void set(double e, double2 x) {
+    re = e * x.x;
+    im = e * x.y;
+  }
+  __device__ __forceinline__ void mac(double cr, double ci, double2 x) {
+    re = fma(cr, x.x, re);
+    re = fma(-ci, x.y, re);
+    im = fma(cr, x.y, im);
+    im = fma(ci, x.x, im);
+  }
+  __device__ __forceinline__ void mac_re(double cr, double2 x) {
+    re = fma(cr, x.x, re);
+    im = fma(cr, x.y, im);
+  }
+  __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
+};
+
+template <typename real>
+__device__ __forceinline__ typename Cx<real>::v2 ldx(const void* x, long long idx) {
+  return __ldg(reinterpret_cast<const typename Cx<real>::v2*>(x) + idx);
+}
+
+// RS > 0: the row stride R is the compile-time constant RS (gathers use
+// immediate offsets); RS = 0: runtime R.
+template <typename real, int K, int MODE, int RS>
 __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ LaunchArgs a) {
+  using v2 = typename Cx<real>::v2;
   constexpr int NR = 1 << K;
   constexpr bool kPartials = MODE == kModeLanczos;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -92,7 +145,9 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
   const int Rg = a.Rg;
   const int kl = threadIdx.x % Rg;
   const int slot = threadIdx.x / Rg, slots = bd / Rg;
-  const int R = a.R;
+  const int R = RS > 0 ? RS : a.R;
+  // real s+ s- coefficients and warp-uniform row bits (a warp serves one cube)
+  const bool real_fast = a.real_pm && (Rg % 32 == 0);
 
   // ---- per-system tables ----
   for (int q = threadIdx.x; q < n * n; q += bd) {
@@ -200,11 +255,12 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
     real pacc[3] = {0, 0, 0};
     for (int g = slot; g < Gt; g += slots) {
       const long long mu0 = row0 + ((long long)g << K);
-      if (mu0 >= d.dim) break;
+      if (mu0 >= d.dim) break;  // ragged last tile (d is a multiple of 2^K)
       const void* x = d.x;
-      real xr[NR], xi[NR], ar[NR], ai[NR];
+      v2 xo[NR];
+      Cx<real> acc[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) VecIO<real, 1>::ldg(x, (mu0 + r) * R + k, &xr[r], &xi[r]);
+      for (int r = 0; r < NR; ++r) xo[r] = ldx<real>(x, (mu0 + r) * R + k);
       // diagonal
       {
         const real eh = S.ehi[g];
@@ -216,20 +272,18 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
           real e = eh + S.ecube[r];
 #pragma unroll
           for (int c = 0; c < K; ++c) e += ((r >> c) & 1) ? (real)0.5 * gzc[c] : (real)-0.5 * gzc[c];
-          ar[r] = e * xr[r];
-          ai[r] = e * xi[r];
+          acc[r].set(e, xo[r]);
         }
       }
       // flips of cube bits: single flips and pairs, all in registers
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const real fhr = S.fhi[2 * (c * Gt + g)], fhi_ = S.fhi[2 * (c * Gt + g) + 1];
+        const real fhr = S.fhi[2 * (c * Gt + g)], fhim = S.fhi[2 * (c * Gt + g) + 1];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const real fr = fhr + S.fcube[2 * (c * NR + r)];
-          const real fi = ((r >> c) & 1) ? fhi_ + S.fcube[2 * (c * NR + r) + 1] : -(fhi_ + S.fcube[2 * (c * NR + r) + 1]);
-          const int nb = r ^ (1 << c);
-          cmac<real, 1>(&ar[r], &ai[r], fr, fi, &xr[nb], &xi[nb]);
+          const real fim = fhim + S.fcube[2 * (c * NR + r) + 1];
+          acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
         }
 #pragma unroll
         for (int c1 = 0; c1 < c; ++c1) {
@@ -237,8 +291,7 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             const int idx = 2 * ((r >> c1) & 1) + ((r >> c) & 1);
-            const int nb = r ^ (1 << c) ^ (1 << c1);
-            cmac<real, 1>(&ar[r], &ai[r], cp[2 * idx], cp[2 * idx + 1], &xr[nb], &xi[nb]);
+            acc[r].mac(cp[2 * idx], cp[2 * idx + 1], xo[r ^ (1 << c) ^ (1 << c1)]);
           }
         }
       }
@@ -246,26 +299,34 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
       for (int j = K; j < n; ++j) {
         const int bj = (int)((mu0 >> j) & 1);
         const long long nb0 = mu0 ^ (1ll << j);
-        real yr[NR], yi[NR];
+        v2 y[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) VecIO<real, 1>::ldg(x, (nb0 + r) * R + k, &yr[r], &yi[r]);
-        const real fhr = S.fhi[2 * (j * Gt + g)], fhi_ = S.fhi[2 * (j * Gt + g) + 1];
+        for (int r = 0; r < NR; ++r) y[r] = ldx<real>(x, (nb0 + r) * R + k);
+        const real fhr = S.fhi[2 * (j * Gt + g)], fhim = S.fhi[2 * (j * Gt + g) + 1];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const real fr = fhr + S.fcube[2 * (j * NR + r)];
-          const real fim = fhi_ + S.fcube[2 * (j * NR + r) + 1];
-          cmac<real, 1>(&ar[r], &ai[r], fr, bj ? fim : -fim, &yr[r], &yi[r]);
+          const real fim = fhim + S.fcube[2 * (j * NR + r) + 1];
+          acc[r].mac(fr, bj ? fim : -fim, y[r]);
         }
 #pragma unroll
         for (int c = 0; c < K; ++c) {
           const real* cp = S.cp + tri(c, j) * 8;
           const real c0r = cp[2 * bj], c0i = cp[2 * bj + 1];            // bit c of the row = 0
           const real c1r = cp[2 * (2 + bj)], c1i = cp[2 * (2 + bj) + 1];  // bit c of the row = 1
+          if (real_fast) {  // one of the two is an s+ s- coefficient: real
 #pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            const int nb = r ^ (1 << c);
-            if ((r >> c) & 1) cmac<real, 1>(&ar[r], &ai[r], c1r, c1i, &yr[nb], &yi[nb]);
-            else cmac<real, 1>(&ar[r], &ai[r], c0r, c0i, &yr[nb], &yi[nb]);
+            for (int r = 0; r < NR; ++r) {
+              const int bc = (r >> c) & 1;
+              if (bc != bj) acc[r].mac_re(bc ? c1r : c0r, y[r ^ (1 << c)]);
+              else acc[r].mac(bc ? c1r : c0r, bc ? c1i : c0i, y[r ^ (1 << c)]);
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              if ((r >> c) & 1) acc[r].mac(c1r, c1i, y[r ^ (1 << c)]);
+              else acc[r].mac(c0r, c0i, y[r ^ (1 << c)]);
+            }
           }
         }
       }
@@ -273,16 +334,21 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
       for (int j = K + 1; j < n; ++j) {
         const int bj = (int)((mu0 >> j) & 1);
         const real* cpj = S.cp + tri(K, j) * 8 + 2 * bj;
+#pragma unroll 2
         for (int i = K; i < j; ++i) {
           const int bi = (int)((mu0 >> i) & 1);
           const real* cp = cpj + (i - K) * 8 + 4 * bi;
           const real cr = cp[0], ci = cp[1];
           const long long nb0 = mu0 ^ (1ll << j) ^ (1ll << i);
+          v2 y[NR];
 #pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            real yr, yi;
-            VecIO<real, 1>::ldg(x, (nb0 + r) * R + k, &yr, &yi);
-            cmac<real, 1>(&ar[r], &ai[r], cr, ci, &yr, &yi);
+          for (int r = 0; r < NR; ++r) y[r] = ldx<real>(x, (nb0 + r) * R + k);
+          if (real_fast && bi != bj) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r].mac_re(cr, y[r]);
+          } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r].mac(cr, ci, y[r]);
           }
         }
       }
@@ -290,23 +356,25 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const long long idx = (mu0 + r) * R + k;
+        const v2 hv = acc[r].value();
+        v2* yp = reinterpret_cast<v2*>(d.y) + idx;
         if (MODE == kModeApply) {
-          VecIO<real, 1>::st(d.y, idx, &ar[r], &ai[r]);
+          __stcs(yp, hv);
         } else {
-          real wr = sig * ar[r], wi = sig * ai[r];
+          v2 w;
+          w.x = sig * hv.x;
+          w.y = sig * hv.y;
           if (!a.first) {
-            real qr, qi;
-            VecIO<real, 1>::ld(d.y, idx, &qr, &qi);
-            wr = fma(-bsp, qr, wr);
-            wi = fma(-bsp, qi, wi);
+            const v2 q = __ldcs(yp);
+            w.x = fma(-bsp, q.x, w.x);
+            w.y = fma(-bsp, q.y, w.y);
           }
-          VecIO<real, 1>::st(d.y, idx, &wr, &wi);
-          real ur, ui;
-          VecIO<real, 1>::ldg(d.u, idx, &ur, &ui);
-          const real vr = sig * xr[r], vi = sig * xi[r];
-          pacc[0] += vr * wr + vi * wi;
-          pacc[1] += vr * ur + vi * ui;
-          pacc[2] += vr * ui - vi * ur;
+          __stcs(yp, w);
+          const v2 u = __ldcs(reinterpret_cast<const v2*>(d.u) + idx);
+          const real vr = sig * xo[r].x, vi = sig * xo[r].y;
+          pacc[0] += vr * w.x + vi * w.y;
+          pacc[1] += vr * u.x + vi * u.y;
+          pacc[2] += vr * u.y - vi * u.x;
         }
       }
     }
@@ -338,12 +406,18 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
 }
 
 // ---------------------------------------------------------------------------
-template <typename real, int K>
-static int launch_k(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
-  if (a.mode == kModeApply) half_kernel<real, K, kModeApply><<<grid, threads, smem, st>>>(a);
-  else if (a.mode == kModeLanczos) half_kernel<real, K, kModeLanczos><<<grid, threads, smem, st>>>(a);
+template <typename real, int K, int RS>
+static int launch_krs(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (a.mode == kModeApply) half_kernel<real, K, kModeApply, RS><<<grid, threads, smem, st>>>(a);
+  else if (a.mode == kModeLanczos) half_kernel<real, K, kModeLanczos, RS><<<grid, threads, smem, st>>>(a);
   else return (int)cudaErrorInvalidValue;
   return (int)cudaGetLastError();
+}
+
+template <typename real, int K>
+static int launch_k(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (a.R == 64) return launch_krs<real, K, 64>(a, grid, threads, smem, st);
+  return launch_krs<real, K, 0>(a, grid, threads, smem, st);
 }
 
 int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size_t smem, void* stream) {
@@ -366,7 +440,8 @@ int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size
 
 template <typename real, int K>
 static int allow_half(int bytes) {
-  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply>, (const void*)half_kernel<real, K, kModeLanczos>};
+  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply, 0>, (const void*)half_kernel<real, K, kModeLanczos, 0>,
+                      (const void*)half_kernel<real, K, kModeApply, 64>, (const void*)half_kernel<real, K, kModeLanczos, 64>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
@@ -388,13 +463,13 @@ int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem) {
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
   if (c64) {
-    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 2, kModeLanczos>, threads, smem);
-    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 3, kModeLanczos>, threads, smem);
-    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 4, kModeLanczos>, threads, smem);
+    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 2, kModeLanczos, 0>, threads, smem);
+    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 3, kModeLanczos, 0>, threads, smem);
+    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 4, kModeLanczos, 0>, threads, smem);
   } else {
-    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 2, kModeLanczos>, threads, smem);
-    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 3, kModeLanczos>, threads, smem);
-    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 4, kModeLanczos>, threads, smem);
+    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 2, kModeLanczos, 0>, threads, smem);
+    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 3, kModeLanczos, 0>, threads, smem);
+    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 4, kModeLanczos, 0>, threads, smem);
   }
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
