@@ -148,6 +148,32 @@ ftlm_status ftlm_apply_sdir(const ftlm_system* sys, const double* u, const void*
 ftlm_status ftlm_start_block(const ftlm_system* sys, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
                              ftlm_dtype dtype, void* stream);
 
+/*
+ * ftlm_start_block_noalloc -- the same normalised Gaussian start block as
+ * ftlm_start_block, for callers that cannot allocate device memory.  Such
+ * callers include code running inside a memory budget that someone else
+ * owns, or a host that may not call cudaMalloc / cudaFree at that point.
+ * This call performs no device allocation and no free, and calls no
+ * allocating library routine.  The paper has no counterpart: it is a
+ * property of this library's interface, not of the method.
+ *
+ * Its scratch (per-CTA partial sums of the vector norms, an arrival counter
+ * and the per-vector scales) is a file-scope device array of 532,544 bytes
+ * that every GPU which loads the library holds until the process exits.
+ *  nvec   1..64: larger blocks are rejected with FTLM_ERR_INVALID_ARG
+ *         (use ftlm_start_block, which allocates).
+ *  The first call on a device looks up the array's device address for that
+ *  device (a CUDA runtime query, not an allocation); make that first call
+ *  before any stream capture.
+ *  All calls on a device share the one array, and it keeps the last call's
+ *  contents.  Calls whose GPU work overlaps (concurrent streams, or several
+ *  host threads) race on it and give wrong results; order them on one
+ *  stream or synchronise between them.
+ * Arguments, layout, alignment and stream behaviour as ftlm_start_block.
+ */
+ftlm_status ftlm_start_block_noalloc(const ftlm_system* sys, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                                     ftlm_dtype dtype, void* stream);
+
 typedef struct {
   int R;                 /* random vectors (block width), >= 1 */
   int M;                 /* Lanczos steps N_L per vector, >= 1 */

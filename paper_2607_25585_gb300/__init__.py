@@ -62,8 +62,8 @@ class Result(ctypes.Structure):
 # every symbol include/ftlm.h declares
 EXPORTS = ["ftlm_system_create", "ftlm_system_destroy", "ftlm_system_dim", "ftlm_system_table_bytes",
            "ftlm_apply_h", "ftlm_apply_sdir",
-           "ftlm_start_block", "ftlm_run", "ftlm_run_batch", "ftlm_sums", "ftlm_tune_shape", "ftlm_last_error",
-           "ftlm_version"]
+           "ftlm_start_block", "ftlm_start_block_noalloc", "ftlm_run", "ftlm_run_batch", "ftlm_sums",
+           "ftlm_tune_shape", "ftlm_last_error", "ftlm_version"]
 
 _lib = None
 
@@ -92,6 +92,7 @@ def lib():
         L.ftlm_apply_h.argtypes = [vp, vp, vp, i, i, vp]
         L.ftlm_apply_sdir.argtypes = [vp, pd, vp, vp, i, i, vp]
         L.ftlm_start_block.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp, i, i, vp]
+        L.ftlm_start_block_noalloc.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp, i, i, vp]
         L.ftlm_run.argtypes = [vp, P(RunParams), P(Result)]
         L.ftlm_run_batch.argtypes = [i, P(vp), P(RunParams), P(Result)]
         L.ftlm_sums.argtypes = [i, i, P(i), pd, pd, pd, d, d, pd, i, P(Result)]
@@ -99,7 +100,7 @@ def lib():
         L.ftlm_last_error.restype = ctypes.c_char_p
         L.ftlm_version.restype = ctypes.c_char_p
         for f in ("ftlm_system_create", "ftlm_apply_h", "ftlm_apply_sdir", "ftlm_start_block", "ftlm_run",
-                  "ftlm_run_batch", "ftlm_sums", "ftlm_tune_shape"):
+                  "ftlm_run_batch", "ftlm_sums", "ftlm_tune_shape", "ftlm_start_block_noalloc"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -213,6 +214,15 @@ def start_block(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dty
     """Normalised Gaussian start vectors into a device block (``ftlm_start_block``)."""
     _check(lib().ftlm_start_block(sys.handle, int(seed), int(vec_offset), _ptr(out), int(nvec), _DTYPES[dtype],
                                   _stream(stream, out)))
+
+
+def start_block_noalloc(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dtype="c64", stream=None):
+    """``ftlm_start_block`` without any device allocation, for callers that
+    may not allocate (``ftlm_start_block_noalloc``): its scratch is a static
+    device array inside the library, so at most 64 vectors, and calls that
+    overlap on the GPU race on that array."""
+    _check(lib().ftlm_start_block_noalloc(sys.handle, int(seed), int(vec_offset), _ptr(out), int(nvec),
+                                          _DTYPES[dtype], _stream(stream, out)))
 
 
 def _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, obs_dir, breakdown_tol, autotune,

@@ -695,12 +695,84 @@ ftlm_status rows_entry(const ftlm_system* cs, int mode, const double* u, const v
   return FTLM_OK;
 }
 
+// ---- the allocation-free start block ------------------------------------------
+//
+// Scratch of ftlm_start_block_noalloc: a file-scope device array instead of
+// cudaMalloc.  Layout (doubles): [0, 8) arrival counter; then the per-vector
+// scalars of a one-step run (alpha, beta, p, sigma, scale, active, M_eff);
+// then the per-CTA partial sums [kNoAllocMaxCtas][kNoAllocMaxVectors][kNumPartials].
+constexpr int kNoAllocMaxVectors = 64;
+constexpr int kNoAllocMaxCtas = 256;
+constexpr size_t kNoAllocScalars = 16 * (size_t)kNoAllocMaxVectors;
+constexpr size_t kNoAllocDoubles = 8 + kNoAllocScalars + (size_t)kNoAllocMaxCtas * kNoAllocMaxVectors * kNumPartials;
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of the array, per device
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // exported entry points
 // ---------------------------------------------------------------------------
 extern "C" {
+
+ftlm_status ftlm_start_block_noalloc(const ftlm_system* cs, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                                     ftlm_dtype dtype, void* stream) {
+  ftlm_status v = check_block_args(cs, out, out, nvec, dtype);
+  if (v != FTLM_OK) return v;
+  if (nvec > kNoAllocMaxVectors)
+    return fail(FTLM_ERR_INVALID_ARG, "ftlm_start_block_noalloc: nvec " + std::to_string(nvec) +
+                                          " exceeds the static scratch (at most " +
+                                          std::to_string(kNoAllocMaxVectors) + " vectors)");
+  const int c64 = dtype == FTLM_C64;
+  ftlm_system* s = const_cast<ftlm_system*>(cs);
+  std::lock_guard<std::mutex> lk(s->mu);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(FTLM_ERR_UNSUPPORTED, "device ordinal too large");
+  void* base = nullptr;
+  {
+    // once per device, with that device current: the host-side name of the
+    // array is not a device address, so ask the runtime for it
+    std::lock_guard<std::mutex> l2(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  double* scratch = reinterpret_cast<double*>(base);
+  unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+  double* scal = scratch + 8;
+  double* partials = scal + kNoAllocScalars;
+  cudaStream_t st = pick_stream(s, stream);
+  Plan pl;
+  std::vector<ftlm_system*> one{s};
+  ftlm_status ps = make_plan(one, nvec, c64, pl);
+  if (ps != FTLM_OK) return ps;
+  const int grid = std::min(pl.grid, kNoAllocMaxCtas);
+  // the arrival counter must start at zero; everything else is overwritten
+  CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+  InstDesc h = base_desc(s, c64);
+  CKI(launch_start_random(&h, nullptr, nvec, seed, vec_offset, out, c64, st));
+  LaunchArgs a = pl.base;
+  a.inline_one = 1;
+  a.one = h;
+  a.one.x = out;
+  a.one.y = out;
+  a.one.M = 1;
+  a.one.sc = scalars_at(scal, nvec, 1);
+  a.partials = partials;
+  a.counter = counter;
+  a.mode = kModeStartNorm;
+  CKI(launch_rows(a, c64, grid, pl.sh.threads, pl.smem, st));
+  a.mode = kModeScale;
+  CKI(launch_rows(a, c64, grid, pl.sh.threads, pl.smem, st));
+  return FTLM_OK;
+}
 
 ftlm_status ftlm_system_create(int n_sites, const int* two_s, const double* J, const double* d_ion,
                                const double* e_axes, double g, const double B[3], const double* pos,
