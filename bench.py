@@ -130,7 +130,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     kw = dict(R=R, M=M, T=T, seed=spec["seed"], vec_offset=rank * R, dtype="c64", stream=stream,
               time_kernels=True)
-    F.run(s, autotune=True, **kw)          # tunes launch shapes, captures the graph
+    if args.shape:
+        F.tune_shape(s, R, "c64", *[int(v) for v in args.shape.split(",")])
+        F.run(s, **kw)                     # captures the graph
+    else:
+        F.run(s, autotune=True, **kw)      # tunes launch shapes, captures the graph
     for _ in range(args.warmup):
         F.run(s, **kw)
     sampler = ClockSampler(local)
@@ -208,7 +212,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "rows_kernel<float,2,Lanczos> (fused H.v step)",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": traffic, "algorithmic_flops_per_sv": flops_sv,
-                         "hv_ms_per_launch": hv_per_launch_ms,
+                         "hv_ms_per_launch": hv_per_launch_ms, "launch_shape": results["shape"],
                          "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"},
             "hbm": {"bytes_per_sv": 32, "peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                     "frac": value / ws * 32 / (hbm * 1e9)},
@@ -338,6 +342,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--hv-only", type=int, default=0, help="time N launches of the H.v kernel alone")
+    ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes instead of autotuning")
     args = ap.parse_args()
     if args.hv_only:
         print(json.dumps(run_hv_only(args)), flush=True)

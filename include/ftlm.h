@@ -212,6 +212,12 @@ typedef struct {
   int kernel_launches;    /* all kernel launches in the run */
   uint64_t h2d_bytes;     /* host-to-device bytes copied by the run */
   uint64_t d2h_bytes;     /* device-to-host bytes copied by the run */
+  /* launch shape of the H.v launches (see ftlm_tune_shape) */
+  int cube_bits;          /* 0: general row kernel; 2..4: spin-1/2 register cubes */
+  int group_vectors;      /* register-cube kernel: vectors per group */
+  int tile_rows;          /* rows per tile */
+  int grid;               /* CTAs per H.v launch */
+  int threads;            /* threads per CTA */
 } ftlm_result;
 
 /*

@@ -56,6 +56,8 @@ class Result(ctypes.Structure):
         ("M_eff", ctypes.POINTER(ctypes.c_int)), ("E0", ctypes.c_double), ("device_ms", ctypes.c_double),
         ("hv_ms", ctypes.c_double), ("hv_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
         ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+        ("cube_bits", ctypes.c_int), ("group_vectors", ctypes.c_int), ("tile_rows", ctypes.c_int),
+        ("grid", ctypes.c_int), ("threads", ctypes.c_int),
     ]
 
 
@@ -249,7 +251,9 @@ def _result(R, M, nT, keep):
 
 def _finish(r, out):
     out.update(E0=r.E0, device_ms=r.device_ms, hv_ms=r.hv_ms, hv_launches=r.hv_launches,
-               kernel_launches=r.kernel_launches, h2d_bytes=int(r.h2d_bytes), d2h_bytes=int(r.d2h_bytes))
+               kernel_launches=r.kernel_launches, h2d_bytes=int(r.h2d_bytes), d2h_bytes=int(r.d2h_bytes),
+               shape={"cube_bits": r.cube_bits, "group_vectors": r.group_vectors, "tile_rows": r.tile_rows,
+                      "grid": r.grid, "threads": r.threads})
     return out
 
 

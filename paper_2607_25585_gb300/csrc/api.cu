@@ -81,6 +81,7 @@ struct ftlm_system {
   uint64_t id = 0;       // unique per system
   uint64_t gen = 0;      // bumped whenever the workspace is reallocated
   DevBuf A, B, U, scal;  // Lanczos workspace: two vector blocks, the observable block, scalars
+  DevBuf Hq;             // H q_j when the gather and the step epilogue are separate launches
   DevBuf ep, ecnt, esc;  // start-block scratch: partials, arrival counter, scalars
   std::mutex mu;
 };
@@ -283,6 +284,16 @@ ftlm_status ensure_workspace(ftlm_system* s, int R, int M, int c64) {
   return FTLM_OK;
 }
 
+ftlm_status ensure_hq(ftlm_system* s, int R, int c64) {
+  const size_t block = (size_t)s->hs.dim * R * (c64 ? 8 : 16);
+  if (s->Hq.bytes < block) {
+    s->Hq.release();
+    CK(s->Hq.ensure(block));
+    s->gen++;
+  }
+  return FTLM_OK;
+}
+
 DevScalars scalars_at(void* base, int R, int M) {
   DevScalars sc;
   double* b = reinterpret_cast<double*>(base);
@@ -396,6 +407,9 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   const InstDesc* d_even = reinterpret_cast<const InstDesc*>(ctx.desc.p);
   const InstDesc* d_odd = d_even + n;
   const InstDesc* d_start = d_even + 2 * n;
+  const InstDesc* d_gather_even = d_even + 3 * n;  // split steps: x = q_j, y = Hq
+  const InstDesc* d_gather_odd = d_even + 4 * n;
+  const bool split = pl.half.on;  // the spin-1/2 gather runs alone; the step epilogue streams afterwards
   LaunchArgs a = pl.base;
   a.tile_start = reinterpret_cast<const int*>(ctx.tiles.p);
   a.partials = reinterpret_cast<double*>(ctx.partials.p);
@@ -427,10 +441,22 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
     a.inst = (j % 2 == 0) ? d_even : d_odd;
     a.step = j;
     a.first = j == 0;
-    a.mode = kModeLanczos;
-    if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
-    CKI(launch_plan(pl, a, st));
-    if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+    if (split) {
+      LaunchArgs g = a;
+      g.inst = (j % 2 == 0) ? d_gather_even : d_gather_odd;
+      g.mode = kModeApply;
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      CKI(launch_plan(pl, g, st));
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      a.mode = kModeEpilogue;
+      CKI(launch_plan(pl, a, st));
+      ctx.launches++;
+    } else {
+      a.mode = kModeLanczos;
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      CKI(launch_plan(pl, a, st));
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+    }
     a.mode = kModeUpdate;
     CKI(launch_plan(pl, a, st));
     ctx.launches += 2;
@@ -451,8 +477,9 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
                       cudaStream_t st) {
   const int c64 = pl.c64, R = p->R, M = p->M, n = (int)sys.size();
   for (auto* s : sys) c.deps.push_back(s->id);
-  // descriptors: even steps (x = A, y = B), odd steps (x = B, y = A), start (x = A, y = U)
-  std::vector<InstDesc> h(3 * n);
+  // descriptors: even steps (x = A, y = B), odd steps (x = B, y = A), start (x = A, y = U),
+  // and for split steps the gathers (x = A or B, y = Hq)
+  std::vector<InstDesc> h(5 * n);
   for (int k = 0; k < n; ++k) {
     ftlm_system* s = sys[k];
     InstDesc d = base_desc(s, c64);
@@ -468,9 +495,17 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
     o.y = s->A.p;
     t.x = s->A.p;
     t.y = s->U.p;
+    e.hq = o.hq = s->Hq.p;
+    InstDesc ge = d, go = d;
+    ge.x = s->A.p;
+    ge.y = s->Hq.p;
+    go.x = s->B.p;
+    go.y = s->Hq.p;
     h[k] = e;
     h[n + k] = o;
     h[2 * n + k] = t;
+    h[3 * n + k] = ge;
+    h[4 * n + k] = go;
   }
   CK(c.desc.ensure(sizeof(InstDesc) * h.size()));
   CK(cudaMemcpy(c.desc.p, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice));
@@ -518,6 +553,10 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   Plan pl;
   ftlm_status ps = make_plan(sys, R, c64, pl);
   if (ps != FTLM_OK) return ps;
+  if (pl.half.on) {
+    ftlm_status hs_ = ensure_hq(sys[0], R, c64);
+    if (hs_ != FTLM_OK) return hs_;
+  }
   const std::string key = run_key(sys, p, pl);
   RunCtx* ctx = nullptr;
   size_t h2d = 0;
@@ -589,6 +628,11 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     out.kernel_launches = ctx->launches;
     out.h2d_bytes = k == 0 ? h2d : 0;
     out.d2h_bytes = per;
+    out.cube_bits = pl.half.on ? pl.half.K : 0;
+    out.group_vectors = pl.half.on ? pl.half.Rg : R;
+    out.tile_rows = pl.half.on ? pl.half.rows_per_tile : pl.sh.rows_per_tile;
+    out.grid = pl.half.on ? pl.half.grid : pl.grid;
+    out.threads = pl.half.on ? pl.half.threads : pl.sh.threads;
   }
   return FTLM_OK;
 }
@@ -823,7 +867,7 @@ void ftlm_system_destroy(ftlm_system* s) {
   cudaDeviceSynchronize();  // the system's buffers may be in use on any stream
   purge_ctx_of(s->id);
   for (DevBuf* b : {&s->tab_f, &s->tab_d, &s->stride, &s->q, &s->A, &s->B, &s->U, &s->scal, &s->ep, &s->ecnt,
-                    &s->esc})
+                    &s->esc, &s->Hq})
     b->release();
   cudaEventDestroy(s->ev_in);
   cudaEventDestroy(s->ev_out);

@@ -110,7 +110,7 @@ __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
     const InstDesc& d = inst_all[inst];
     const DevScalars& sc = d.sc;
     const int j = a.step;
-    if (a.mode == kModeLanczos) {
+    if (a.mode == kModeLanczos || a.mode == kModeEpilogue) {
       const double al = total_partial(a, inst, r, 0);
       const double pr = total_partial(a, inst, r, 1);
       const double pi = total_partial(a, inst, r, 2);

@@ -88,6 +88,7 @@ struct InstDesc {
   const void* x = nullptr;   // gather source (q_j), [dim][R]
   void* y = nullptr;         // output (or in place w over q_{j-1})
   const void* u = nullptr;   // observable vector u.S v_0, [dim][R] (Lanczos steps)
+  const void* hq = nullptr;  // H q_j written by a separate gather launch (kModeEpilogue)
   DevScalars sc;
   double tol = 0.0;          // breakdown tolerance
   int M = 0;
@@ -101,6 +102,7 @@ enum KernelMode : int {
   kModeStartNorm = 3, // partials |x|^2, then sigma_0 = 1/|x|
   kModeApplyS = 4,    // y = scale * (u.S) x  (scale = sigma_0 when Lanczos)
   kModeScale = 5,     // y = sigma_0 x (elementwise; y may equal x)
+  kModeEpilogue = 6,  // as kModeLanczos with H q_j read from `hq` instead of gathered (elementwise)
 };
 
 struct LaunchArgs {

@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
   const SmemView s = carve<real>(smem_raw, a, V);
   __shared__ InstDesc d;
   __shared__ int is_last;
-  constexpr bool kPartials = MODE == kModeLanczos || MODE == kModeUpdate || MODE == kModeStartNorm;
+  constexpr bool kPartials =
+      MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate || MODE == kModeStartNorm;
   const InstDesc* insts = a.inline_one ? &a.one : a.inst;
   constexpr int NP = V * kNumPartials;
   double acc[NP];
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
       for (int v = 0; v < V; ++v) {
         const int k = min(col + v, a.R - 1);
         sig[v] = bsp[v] = coef[v] = 0;
-        if (MODE == kModeLanczos) {
+        if (MODE == kModeLanczos || MODE == kModeEpilogue) {
           sig[v] = (real)d.sc.sigma[(size_t)j * a.R + k];
           if (!a.first) bsp[v] = (real)(d.sc.beta[(size_t)(j - 1) * a.R + k] * d.sc.sigma[(size_t)(j - 1) * a.R + k]);
         } else if (MODE == kModeUpdate) {
@@ -306,9 +307,14 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
       const long long row = row0 + item / C;
       if (row >= d.dim) break;
       const long long idx = row * a.R + col;
-      if (MODE == kModeApply || MODE == kModeLanczos) {
+      if (MODE == kModeApply || MODE == kModeLanczos || MODE == kModeEpilogue) {
         real ar[V], ai[V], xr[V], xi[V];
-        h_row<real, V>(s, d.lay, d.n, row, idx32, d.x, a.R, col, ar, ai, xr, xi);
+        if (MODE == kModeEpilogue) {  // H q_j from the gather launch, own row of q_j
+          VecIO<real, V>::ldg(d.hq, idx, ar, ai);
+          VecIO<real, V>::ldg(d.x, idx, xr, xi);
+        } else {
+          h_row<real, V>(s, d.lay, d.n, row, idx32, d.x, a.R, col, ar, ai, xr, xi);
+        }
         if (MODE == kModeApply) {
           VecIO<real, V>::st(d.y, idx, ar, ai);
         } else {
@@ -478,7 +484,8 @@ template <typename real, int V>
 static int allow_smem(int bytes) {
   const void* ks[] = {(const void*)rows_kernel<real, V, kModeApply>, (const void*)rows_kernel<real, V, kModeLanczos>,
                       (const void*)rows_kernel<real, V, kModeUpdate>, (const void*)rows_kernel<real, V, kModeStartNorm>,
-                      (const void*)rows_kernel<real, V, kModeApplyS>, (const void*)rows_kernel<real, V, kModeScale>};
+                      (const void*)rows_kernel<real, V, kModeApplyS>, (const void*)rows_kernel<real, V, kModeScale>,
+                      (const void*)rows_kernel<real, V, kModeEpilogue>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
@@ -504,6 +511,7 @@ static int launch_mode(const LaunchArgs& a, int grid, int threads, size_t smem, 
     case kModeStartNorm: return launch_one<real, V, kModeStartNorm>(a, grid, threads, smem, st);
     case kModeApplyS: return launch_one<real, V, kModeApplyS>(a, grid, threads, smem, st);
     case kModeScale: return launch_one<real, V, kModeScale>(a, grid, threads, smem, st);
+    case kModeEpilogue: return launch_one<real, V, kModeEpilogue>(a, grid, threads, smem, st);
     default: return (int)cudaErrorInvalidValue;
   }
 }
