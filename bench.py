@@ -342,7 +342,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--hv-only", type=int, default=0, help="time N launches of the H.v kernel alone")
-    ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes instead of autotuning")
+    ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] instead of autotuning")
     args = ap.parse_args()
     if args.hv_only:
         print(json.dumps(run_hv_only(args)), flush=True)

@@ -214,6 +214,7 @@ typedef struct {
   uint64_t d2h_bytes;     /* device-to-host bytes copied by the run */
   /* launch shape of the H.v launches (see ftlm_tune_shape) */
   int cube_bits;          /* 0: general row kernel; 2..4: spin-1/2 register cubes */
+  int passes;             /* launches per H.v (spin-1/2 multi-pass form: ceil(n / cube_bits)) */
   int group_vectors;      /* register-cube kernel: vectors per group */
   int tile_rows;          /* rows per tile */
   int grid;               /* CTAs per H.v launch */
@@ -268,10 +269,15 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
  *                 gathered slice of the block is d * group_vectors elements),
  *                 1..min(nvec, 256).
  *  tile_cubes     register-cube kernel: cubes per thread slot in a row tile, 1..64.
+ *  multipass      register-cube kernel: 0 = one launch whose cube is the low
+ *                 cube_bits bits; 1 = ceil(n / cube_bits) launches whose cubes
+ *                 cover all bits, so every pair is a cube or cube-neighbour
+ *                 pair of one launch (fewer gathered loads, the output is
+ *                 re-read by every launch after the first).
  * Host-only; returns FTLM_ERR_UNSUPPORTED for cube_bits > 0 on other spins.
  */
 ftlm_status ftlm_tune_shape(const ftlm_system* sys, int nvec, ftlm_dtype dtype, int cube_bits, int group_vectors,
-                            int tile_cubes);
+                            int tile_cubes, int multipass);
 
 const char* ftlm_last_error(void);
 const char* ftlm_version(void);

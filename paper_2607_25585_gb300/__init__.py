@@ -56,7 +56,8 @@ class Result(ctypes.Structure):
         ("M_eff", ctypes.POINTER(ctypes.c_int)), ("E0", ctypes.c_double), ("device_ms", ctypes.c_double),
         ("hv_ms", ctypes.c_double), ("hv_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
         ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-        ("cube_bits", ctypes.c_int), ("group_vectors", ctypes.c_int), ("tile_rows", ctypes.c_int),
+        ("cube_bits", ctypes.c_int), ("passes", ctypes.c_int), ("group_vectors", ctypes.c_int),
+        ("tile_rows", ctypes.c_int),
         ("grid", ctypes.c_int), ("threads", ctypes.c_int),
     ]
 
@@ -98,7 +99,7 @@ def lib():
         L.ftlm_run.argtypes = [vp, P(RunParams), P(Result)]
         L.ftlm_run_batch.argtypes = [i, P(vp), P(RunParams), P(Result)]
         L.ftlm_sums.argtypes = [i, i, P(i), pd, pd, pd, d, d, pd, i, P(Result)]
-        L.ftlm_tune_shape.argtypes = [vp, i, i, i, i, i]
+        L.ftlm_tune_shape.argtypes = [vp, i, i, i, i, i, i]
         L.ftlm_last_error.restype = ctypes.c_char_p
         L.ftlm_version.restype = ctypes.c_char_p
         for f in ("ftlm_system_create", "ftlm_apply_h", "ftlm_apply_sdir", "ftlm_start_block", "ftlm_run",
@@ -252,7 +253,8 @@ def _result(R, M, nT, keep):
 def _finish(r, out):
     out.update(E0=r.E0, device_ms=r.device_ms, hv_ms=r.hv_ms, hv_launches=r.hv_launches,
                kernel_launches=r.kernel_launches, h2d_bytes=int(r.h2d_bytes), d2h_bytes=int(r.d2h_bytes),
-               shape={"cube_bits": r.cube_bits, "group_vectors": r.group_vectors, "tile_rows": r.tile_rows,
+               shape={"cube_bits": r.cube_bits, "passes": r.passes, "group_vectors": r.group_vectors,
+                      "tile_rows": r.tile_rows,
                       "grid": r.grid, "threads": r.threads})
     return out
 
@@ -307,10 +309,10 @@ def sums(alpha, beta, p, M_eff, dim, g, T) -> dict:
 
 
 def tune_shape(sys: System, nvec: int, dtype="c64", cube_bits: int = 0, group_vectors: int = 1,
-               tile_cubes: int = 2):
+               tile_cubes: int = 2, multipass: int = 0):
     """Override the launch shape for (system shape, nvec, dtype) (``ftlm_tune_shape``)."""
     _check(lib().ftlm_tune_shape(sys.handle, int(nvec), _DTYPES[dtype], int(cube_bits), int(group_vectors),
-                                 int(tile_cubes)))
+                                 int(tile_cubes), int(multipass)))
 
 
 def version() -> str:

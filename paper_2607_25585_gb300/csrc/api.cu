@@ -148,6 +148,7 @@ InstDesc base_desc(const ftlm_system* s, int c64) {
 struct HalfPlan {
   bool on = false;
   int real_pm = 0;
+  int passes = 1;  // > 1: one launch per pass, cubes covering all bits
   int K = 3, Rg = 1, threads = 256, rows_per_tile = 0, grid = 0, nvg = 0, tiles_per_vg = 0;
   size_t smem = 0;
 };
@@ -170,12 +171,13 @@ int largest_divisor_at_most(int R, int cap) {
 
 // Spin-1/2 register-cube launch: K cube bits, Rg vectors per group, tile of
 // rows_factor cubes per slot.
-bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_factor, HalfPlan& h) {
+bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_factor, bool multipass, HalfPlan& h) {
   const HostSystem& hs = s->hs;
   if (!hs.all_half || hs.n < K + 2 || K < 2 || K > 4 || Rg < 1 || Rg > R) return false;
   h = HalfPlan();
   h.K = K;
   h.Rg = Rg;
+  h.passes = multipass ? (hs.n + K - 1) / K : 1;
   h.real_pm = hs.real_pm ? 1 : 0;
   const int slots = std::max(1, 256 / Rg);
   h.threads = slots * Rg;
@@ -239,23 +241,39 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   pl.base = a;
   pl.half.on = false;
   if (sys.size() == 1 && pl.sh.half_K > 0)
-    make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.half);
+    make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.sh.half_multipass != 0, pl.half);
   else if (sys.size() == 1 && !force && !pl.sh.explicit_general && sys[0]->hs.all_half)
-    make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 64), 2, pl.half);
+    make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 16), 4, false, pl.half);
   return FTLM_OK;
 }
 
 // Launches one mode of the plan: the spin-1/2 kernel for H.v modes when the
 // plan has it, the general row kernel otherwise.
 int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
-  if (pl.half.on && (a.mode == kModeApply || a.mode == kModeLanczos)) {
+  const bool half = pl.half.on && (a.mode == kModeApply || (a.mode == kModeLanczos && pl.half.passes == 1));
+  if (half) {
     a.rows_per_tile = pl.half.rows_per_tile;
     a.Rg = pl.half.Rg;
     a.nvg = pl.half.nvg;
     a.tiles_per_vg = pl.half.tiles_per_vg;
     a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
     a.real_pm = pl.half.real_pm;
-    return launch_half(a, pl.half.K, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+    const int K = pl.half.K;
+    const int n = pl.base.max_n;
+    if (pl.half.passes == 1) {
+      a.single_pass = 1;
+      return launch_half(a, K, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+    }
+    for (int p = 0; p < pl.half.passes; ++p) {  // cubes [min(pK, n-K), +K) cover every bit
+      a.cube_lo = std::min(p * K, n - K);
+      a.new_lo = p * K;
+      a.later_lo = a.cube_lo + K;
+      a.first_pass = p == 0;
+      a.single_pass = 0;
+      const int e = launch_half(a, K, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+      if (e) return e;
+    }
+    return 0;
   }
   return launch_rows(a, pl.c64, pl.grid, pl.sh.threads, pl.smem, st);
 }
@@ -364,8 +382,8 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
            (unsigned long long)p->basis_offset, p->user_start, p->time_kernels, pl.sh.threads, pl.sh.rows_per_tile,
            pl.grid, p->breakdown_tol, u[0], u[1], u[2], p->obs_dir ? 1 : 0, p->stream);
   k += buf;
-  snprintf(buf, sizeof buf, "|half%d K%d Rg%d rpt%d g%d", pl.half.on ? 1 : 0, pl.half.K, pl.half.Rg,
-           pl.half.rows_per_tile, pl.half.grid);
+  snprintf(buf, sizeof buf, "|half%d K%d Rg%d rpt%d g%d P%d", pl.half.on ? 1 : 0, pl.half.K, pl.half.Rg,
+           pl.half.rows_per_tile, pl.half.grid, pl.half.passes);
   return k + buf;
 }
 
@@ -629,6 +647,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     out.h2d_bytes = k == 0 ? h2d : 0;
     out.d2h_bytes = per;
     out.cube_bits = pl.half.on ? pl.half.K : 0;
+    out.passes = pl.half.on ? pl.half.passes : 1;
     out.group_vectors = pl.half.on ? pl.half.Rg : R;
     out.tile_rows = pl.half.on ? pl.half.rows_per_tile : pl.sh.rows_per_tile;
     out.grid = pl.half.on ? pl.half.grid : pl.grid;
@@ -652,15 +671,17 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
       const int g = largest_divisor_at_most(R, cap);
       if (std::find(rgs.begin(), rgs.end(), g) == rgs.end()) rgs.push_back(g);
     }
-    for (int K : {2, 3, 4})
-      for (int rg : rgs)
-        for (int f : {1, 4}) {  // cubes per thread slot in a row tile
-          Shape sh = default_shape(R, c64);
-          sh.half_K = K;
-          sh.Rg = rg;
-          sh.half_rows = f;
-          if (s->hs.n >= K + 2) cands.push_back(sh);
-        }
+    for (int mp : {0, 1})
+      for (int K : {3, 4})
+        for (int rg : rgs)
+          for (int f : {1, 4}) {  // cubes per thread slot in a row tile
+            Shape sh = default_shape(R, c64);
+            sh.half_K = K;
+            sh.Rg = rg;
+            sh.half_rows = f;
+            sh.half_multipass = mp;
+            if (s->hs.n >= K + 2) cands.push_back(sh);
+          }
   } else {
     for (int thr : {128, 256})
       for (int f : {1, 4}) cands.push_back(shape_for(R, c64, thr, f));
@@ -972,7 +993,7 @@ ftlm_status ftlm_run_batch(int n, const ftlm_system* const* systems, const ftlm_
 }
 
 ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, int cube_bits, int group_vectors,
-                            int tile_cubes) {
+                            int tile_cubes, int multipass) {
   if (!s) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
   if (dtype != FTLM_C64 && dtype != FTLM_C128) return fail(FTLM_ERR_INVALID_ARG, "unknown dtype");
   const int c64 = dtype == FTLM_C64;
@@ -995,6 +1016,7 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     sh.half_K = cube_bits;
     sh.Rg = group_vectors;
     sh.half_rows = tile_cubes;
+    sh.half_multipass = multipass ? 1 : 0;
   }
   std::lock_guard<std::mutex> lk(g_mu);
   g_shapes[key] = sh;

@@ -129,6 +129,12 @@ struct LaunchArgs {
   int nvg = 0;          // number of vector groups = ceil(R / Rg)
   int tiles_per_vg = 0; // row tiles per vector group
   int real_pm = 0;      // every s+ s- coefficient is real (symmetric coupling tensors)
+  // pass of the spin-1/2 kernel: the register cube spans bits [cube_lo, cube_lo + K)
+  int cube_lo = 0;      // first bit of the cube
+  int new_lo = 0;       // cube bits >= new_lo are this pass's own (their single flips and pairs)
+  int later_lo = 0;     // bits >= later_lo outside the cube: partners of the mixed pairs
+  int first_pass = 1;   // 1: diagonal, and the output is written; 0: the output is accumulated
+  int single_pass = 1;  // 1: the single-pass form (cube on the low K bits, all flags implied)
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -139,6 +145,7 @@ struct Shape {
   int half_K = 0;       // > 0: spin-1/2 register-cube kernel with cubes of 2^half_K rows
   int Rg = 0;           // spin-1/2 kernel: vectors per group
   int half_rows = 2;    // spin-1/2 kernel: cubes per thread slot in a row tile
+  int half_multipass = 0;  // spin-1/2 kernel: 1 = ceil(N/K) passes whose cubes cover all bits
   bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
 };
 

@@ -18,6 +18,14 @@
 // Vector groups.  Vectors are processed Rg at a time (tile order is
 // group-major), so the gathered slice x[:, group] (d * Rg * 8 bytes) stays in
 // L2 while all its neighbours are read.
+//
+// Passes.  With one pass (cube on the low K bits) every pair of two outer
+// bits costs one gathered load per multiply-add.  With ceil(N/K) passes
+// whose cubes cover all N bits, every pair has an endpoint in some cube and
+// is a mixed pair of that pass (K multiply-adds per gathered load); the
+// gathered loads per row drop from 1 + (N-K) + C(N-K, 2) to about
+// N/K + K C(N/K, 2), at the price of re-reading and re-writing the output in
+// every pass after the first.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -124,9 +132,11 @@ __device__ __forceinline__ typename Cx<real>::v2 ldx(const void* x, long long id
   return __ldg(reinterpret_cast<const typename Cx<real>::v2*>(x) + idx);
 }
 
-// RS > 0: the row stride R is the compile-time constant RS (gathers use
-// immediate offsets); RS = 0: runtime R.
-template <typename real, int K, int MODE, int RS>
+// RS > 0: the row stride R is the compile-time constant RS; RS = 0: runtime R.
+// MP: one pass of the multi-pass form (cube position and pass flags from the
+// launch arguments); otherwise the single-pass form with the cube on the low
+// K bits, every choice known at compile time.
+template <typename real, int K, int MODE, int RS, bool MP>
 __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ LaunchArgs a) {
   using v2 = typename Cx<real>::v2;
   constexpr int NR = 1 << K;
@@ -146,6 +156,13 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
   const int kl = threadIdx.x % Rg;
   const int slot = threadIdx.x / Rg, slots = bd / Rg;
   const int R = RS > 0 ? RS : a.R;
+  const int s0 = MP ? a.cube_lo : 0;              // cube bits [s0, s0 + K)
+  const int cnew = MP ? a.new_lo - s0 : 0;        // cube-relative first own bit
+  const bool first = MP ? a.first_pass != 0 : true;
+  const int later_lo = MP ? a.later_lo : K;
+  constexpr bool later_singles = !MP, outer_pairs = !MP;
+  const long long rstep = MP ? ((long long)R << s0) : (long long)R;  // element distance of consecutive cube rows
+  const long long ngroups = d.dim >> K;
   // real s+ s- coefficients and warp-uniform row bits (a warp serves one cube)
   const bool real_fast = a.real_pm && (Rg % 32 == 0);
 
@@ -162,26 +179,28 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
     c[4] = pmr; c[5] = pmi;    // (1,0): mu = s+_i s-_j nu
     c[6] = ppr; c[7] = ppi;    // (1,1): mu = s+_i s+_j nu
   }
-  for (int q = threadIdx.x; q < n * NR; q += bd) {
+  for (int q = threadIdx.x; q < n * NR; q += bd) {  // fcube[j][r] = sum_c rho_{j, s0+c} m_c(r)
     const int j = q / NR, r = q % NR;
     real fr = 0, fi = 0;
     for (int c = 0; c < K; ++c) {
       const real mc = ((r >> c) & 1) ? (real)0.5 : (real)-0.5;
-      fr += t[L.off_rho + 2 * (j * n + c)] * mc;
-      fi += t[L.off_rho + 2 * (j * n + c) + 1] * mc;
+      fr += t[L.off_rho + 2 * (j * n + s0 + c)] * mc;
+      fi += t[L.off_rho + 2 * (j * n + s0 + c) + 1] * mc;
     }
     S.fcube[2 * q] = fr;
     S.fcube[2 * q + 1] = fi;
   }
-  for (int r = threadIdx.x; r < NR; r += bd) {
-    real e = 0;
-    for (int c = 0; c < K; ++c) {
-      const int bc = (r >> c) & 1;
-      const real mc = bc ? (real)0.5 : (real)-0.5;
-      e += t[L.off_hz + c] * mc + t[L.off_iondiag + c * L.qmax + bc];
-      for (int c2 = c + 1; c2 < K; ++c2) e += t[L.off_zz + c * n + c2] * mc * (((r >> c2) & 1) ? (real)0.5 : (real)-0.5);
+  if (first) {  // the diagonal is done by the first pass, whose cube is bits [0, K)
+    for (int r = threadIdx.x; r < NR; r += bd) {
+      real e = 0;
+      for (int c = 0; c < K; ++c) {
+        const int bc = (r >> c) & 1;
+        const real mc = bc ? (real)0.5 : (real)-0.5;
+        e += t[L.off_hz + c] * mc + t[L.off_iondiag + c * L.qmax + bc];
+        for (int c2 = c + 1; c2 < K; ++c2) e += t[L.off_zz + c * n + c2] * mc * (((r >> c2) & 1) ? (real)0.5 : (real)-0.5);
+      }
+      S.ecube[r] = e;
     }
-    S.ecube[r] = e;
   }
 
   double acc_d[4] = {0.0, 0.0, 0.0, 0.0};
@@ -191,9 +210,10 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
   }
   int cur_vg = -1;
   real sig = 0, bsp = 0;
+  const unsigned long long lowmask = (1ull << s0) - 1ull;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int vg = tile / a.tiles_per_vg;
-    const long long row0 = (long long)(tile - vg * a.tiles_per_vg) * a.rows_per_tile;
+    const long long g0 = (long long)(tile - vg * a.tiles_per_vg) * Gt;  // first cube of the tile
     const int k = vg * Rg + kl;
     const bool kvalid = k < R;
     if (vg != cur_vg) {
@@ -219,11 +239,14 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
     }
     __syncthreads();  // the previous tile's cubes are done with fhi / ehi / gz
     // ---- per-tile outer parts ----
-    for (int q = threadIdx.x; q < n * Gt; q += bd) {
+    const int fsites_lo = MP ? a.new_lo : 0, fsites_hi = MP ? s0 + K : n;  // sites whose single flips this pass does
+    for (int q = threadIdx.x + fsites_lo * Gt; q < fsites_hi * Gt; q += bd) {
       const int j = q / Gt, g = q % Gt;
-      const unsigned long long mu0 = (unsigned long long)(row0 + ((long long)g << K));
+      const unsigned long long gi = (unsigned long long)(g0 + g);
+      const unsigned long long mu0 = ((gi >> s0) << (s0 + K)) | (gi & lowmask);
       real fr = t[L.off_hp + 2 * j], fi = t[L.off_hp + 2 * j + 1];
-      for (int i = K; i < n; ++i) {
+      for (int i = 0; i < n; ++i) {
+        if (i >= s0 && i < s0 + K) continue;
         const real mi = ((mu0 >> i) & 1ull) ? (real)0.5 : (real)-0.5;
         fr += t[L.off_rho + 2 * (j * n + i)] * mi;
         fi += t[L.off_rho + 2 * (j * n + i) + 1] * mi;
@@ -231,38 +254,41 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
       S.fhi[2 * q] = fr;
       S.fhi[2 * q + 1] = fi;
     }
-    for (int g = threadIdx.x; g < Gt; g += bd) {
-      const unsigned long long mu0 = (unsigned long long)(row0 + ((long long)g << K));
-      real e = 0;
-      for (int i = K; i < n; ++i) {
-        const int bi = (mu0 >> i) & 1ull;
-        const real mi = bi ? (real)0.5 : (real)-0.5;
-        real zs = t[L.off_hz + i];
-        for (int j = i + 1; j < n; ++j) zs += t[L.off_zz + i * n + j] * (((mu0 >> j) & 1ull) ? (real)0.5 : (real)-0.5);
-        e += mi * zs + t[L.off_iondiag + i * L.qmax + bi];
+    if (first) {
+      for (int g = threadIdx.x; g < Gt; g += bd) {
+        const unsigned long long mu0 = (unsigned long long)(g0 + g) << K;
+        real e = 0;
+        for (int i = K; i < n; ++i) {
+          const int bi = (mu0 >> i) & 1ull;
+          const real mi = bi ? (real)0.5 : (real)-0.5;
+          real zs = t[L.off_hz + i];
+          for (int j = i + 1; j < n; ++j) zs += t[L.off_zz + i * n + j] * (((mu0 >> j) & 1ull) ? (real)0.5 : (real)-0.5);
+          e += mi * zs + t[L.off_iondiag + i * L.qmax + bi];
+        }
+        S.ehi[g] = e;
       }
-      S.ehi[g] = e;
-    }
-    for (int q = threadIdx.x; q < K * Gt; q += bd) {
-      const int c = q / Gt, g = q % Gt;
-      const unsigned long long mu0 = (unsigned long long)(row0 + ((long long)g << K));
-      real zs = 0;
-      for (int i = K; i < n; ++i) zs += t[L.off_zz + c * n + i] * (((mu0 >> i) & 1ull) ? (real)0.5 : (real)-0.5);
-      S.gz[q] = zs;
+      for (int q = threadIdx.x; q < K * Gt; q += bd) {
+        const int c = q / Gt, g = q % Gt;
+        const unsigned long long mu0 = (unsigned long long)(g0 + g) << K;
+        real zs = 0;
+        for (int i = K; i < n; ++i) zs += t[L.off_zz + c * n + i] * (((mu0 >> i) & 1ull) ? (real)0.5 : (real)-0.5);
+        S.gz[q] = zs;
+      }
     }
     __syncthreads();
     if (!kvalid) continue;
     real pacc[3] = {0, 0, 0};
     for (int g = slot; g < Gt; g += slots) {
-      const long long mu0 = row0 + ((long long)g << K);
-      if (mu0 >= d.dim) break;  // ragged last tile (d is a multiple of 2^K)
+      const long long gi = g0 + g;
+      if (gi >= ngroups) break;  // ragged last tile
+      const long long mu0 = (long long)((((unsigned long long)gi >> s0) << (s0 + K)) | ((unsigned long long)gi & lowmask));
       const void* x = d.x;
+      const long long base = mu0 * R + k;
       v2 xo[NR];
       Cx<real> acc[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) xo[r] = ldx<real>(x, (mu0 + r) * R + k);
-      // diagonal
-      {
+      for (int r = 0; r < NR; ++r) xo[r] = ldx<real>(x, base + r * rstep);
+      if (first) {  // diagonal
         const real eh = S.ehi[g];
         real gzc[K];
 #pragma unroll
@@ -274,20 +300,26 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
           for (int c = 0; c < K; ++c) e += ((r >> c) & 1) ? (real)0.5 * gzc[c] : (real)-0.5 * gzc[c];
           acc[r].set(e, xo[r]);
         }
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r].set((real)0, xo[r]);
       }
-      // flips of cube bits: single flips and pairs, all in registers
+      // the pass's own cube bits: single flips and pairs, all in registers
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const real fhr = S.fhi[2 * (c * Gt + g)], fhim = S.fhi[2 * (c * Gt + g) + 1];
+        if (c < cnew) continue;
+        const int sc = s0 + c;
+        const real fhr = S.fhi[2 * (sc * Gt + g)], fhim = S.fhi[2 * (sc * Gt + g) + 1];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          const real fr = fhr + S.fcube[2 * (c * NR + r)];
-          const real fim = fhim + S.fcube[2 * (c * NR + r) + 1];
+          const real fr = fhr + S.fcube[2 * (sc * NR + r)];
+          const real fim = fhim + S.fcube[2 * (sc * NR + r) + 1];
           acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
         }
 #pragma unroll
         for (int c1 = 0; c1 < c; ++c1) {
-          const real* cp = S.cp + tri(c1, c) * 8;
+          if (c1 < cnew) continue;
+          const real* cp = S.cp + tri(s0 + c1, sc) * 8;
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             const int idx = 2 * ((r >> c1) & 1) + ((r >> c) & 1);
@@ -295,23 +327,27 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
           }
         }
       }
-      // outer bit j: the neighbouring cube serves the single flip of j and the mixed pairs (c, j)
-      for (int j = K; j < n; ++j) {
+      // later bit j: the neighbouring cube serves the mixed pairs (c, j) (and, in the
+      // single-pass form, the single flip of j)
+      for (int j = later_lo; j < n; ++j) {
         const int bj = (int)((mu0 >> j) & 1);
-        const long long nb0 = mu0 ^ (1ll << j);
+        const long long nbase = (mu0 ^ (1ll << j)) * R + k;
         v2 y[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) y[r] = ldx<real>(x, (nb0 + r) * R + k);
-        const real fhr = S.fhi[2 * (j * Gt + g)], fhim = S.fhi[2 * (j * Gt + g) + 1];
+        for (int r = 0; r < NR; ++r) y[r] = ldx<real>(x, nbase + r * rstep);
+        if (later_singles) {
+          const real fhr = S.fhi[2 * (j * Gt + g)], fhim = S.fhi[2 * (j * Gt + g) + 1];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const real fr = fhr + S.fcube[2 * (j * NR + r)];
-          const real fim = fhim + S.fcube[2 * (j * NR + r) + 1];
-          acc[r].mac(fr, bj ? fim : -fim, y[r]);
+          for (int r = 0; r < NR; ++r) {
+            const real fr = fhr + S.fcube[2 * (j * NR + r)];
+            const real fim = fhim + S.fcube[2 * (j * NR + r) + 1];
+            acc[r].mac(fr, bj ? fim : -fim, y[r]);
+          }
         }
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          const real* cp = S.cp + tri(c, j) * 8;
+          if (c < cnew) continue;
+          const real* cp = S.cp + tri(s0 + c, j) * 8;
           const real c0r = cp[2 * bj], c0i = cp[2 * bj + 1];            // bit c of the row = 0
           const real c1r = cp[2 * (2 + bj)], c1i = cp[2 * (2 + bj) + 1];  // bit c of the row = 1
           if (real_fast) {  // one of the two is an s+ s- coefficient: real
@@ -330,35 +366,42 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
           }
         }
       }
-      // outer pairs (i, j): one coefficient for the whole cube
-      for (int j = K + 1; j < n; ++j) {
-        const int bj = (int)((mu0 >> j) & 1);
-        const real* cpj = S.cp + tri(K, j) * 8 + 2 * bj;
+      // pairs among the later bits (single-pass form): one coefficient for the whole cube
+      if (outer_pairs) {
+        for (int j = later_lo + 1; j < n; ++j) {
+          const int bj = (int)((mu0 >> j) & 1);
+          const real* cpj = S.cp + tri(later_lo, j) * 8 + 2 * bj;
 #pragma unroll 2
-        for (int i = K; i < j; ++i) {
-          const int bi = (int)((mu0 >> i) & 1);
-          const real* cp = cpj + (i - K) * 8 + 4 * bi;
-          const real cr = cp[0], ci = cp[1];
-          const long long nb0 = mu0 ^ (1ll << j) ^ (1ll << i);
-          v2 y[NR];
+          for (int i = later_lo; i < j; ++i) {
+            const int bi = (int)((mu0 >> i) & 1);
+            const real* cp = cpj + (i - later_lo) * 8 + 4 * bi;
+            const real cr = cp[0], ci = cp[1];
+            const long long nbase = (mu0 ^ (1ll << j) ^ (1ll << i)) * R + k;
+            v2 y[NR];
 #pragma unroll
-          for (int r = 0; r < NR; ++r) y[r] = ldx<real>(x, (nb0 + r) * R + k);
-          if (real_fast && bi != bj) {
+            for (int r = 0; r < NR; ++r) y[r] = ldx<real>(x, nbase + r * rstep);
+            if (real_fast && bi != bj) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r].mac_re(cr, y[r]);
-          } else {
+              for (int r = 0; r < NR; ++r) acc[r].mac_re(cr, y[r]);
+            } else {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r].mac(cr, ci, y[r]);
+              for (int r = 0; r < NR; ++r) acc[r].mac(cr, ci, y[r]);
+            }
           }
         }
       }
       // epilogue
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const long long idx = (mu0 + r) * R + k;
-        const v2 hv = acc[r].value();
+        const long long idx = base + r * rstep;
+        v2 hv = acc[r].value();
         v2* yp = reinterpret_cast<v2*>(d.y) + idx;
         if (MODE == kModeApply) {
+          if (!first) {
+            const v2 prev = __ldcs(yp);
+            hv.x += prev.x;
+            hv.y += prev.y;
+          }
           __stcs(yp, hv);
         } else {
           v2 w;
@@ -408,14 +451,19 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
 // ---------------------------------------------------------------------------
 template <typename real, int K, int RS>
 static int launch_krs(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
-  if (a.mode == kModeApply) half_kernel<real, K, kModeApply, RS><<<grid, threads, smem, st>>>(a);
-  else if (a.mode == kModeLanczos) half_kernel<real, K, kModeLanczos, RS><<<grid, threads, smem, st>>>(a);
+  if (a.mode == kModeApply) half_kernel<real, K, kModeApply, RS, false><<<grid, threads, smem, st>>>(a);
+  else if (a.mode == kModeLanczos) half_kernel<real, K, kModeLanczos, RS, false><<<grid, threads, smem, st>>>(a);
   else return (int)cudaErrorInvalidValue;
   return (int)cudaGetLastError();
 }
 
 template <typename real, int K>
 static int launch_k(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (!a.single_pass) {  // one pass of the multi-pass form (H.v only)
+    if (a.mode != kModeApply) return (int)cudaErrorInvalidValue;
+    half_kernel<real, K, kModeApply, 0, true><<<grid, threads, smem, st>>>(a);
+    return (int)cudaGetLastError();
+  }
   if (a.R == 64) return launch_krs<real, K, 64>(a, grid, threads, smem, st);
   return launch_krs<real, K, 0>(a, grid, threads, smem, st);
 }
@@ -440,8 +488,11 @@ int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size
 
 template <typename real, int K>
 static int allow_half(int bytes) {
-  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply, 0>, (const void*)half_kernel<real, K, kModeLanczos, 0>,
-                      (const void*)half_kernel<real, K, kModeApply, 64>, (const void*)half_kernel<real, K, kModeLanczos, 64>};
+  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply, 0, false>,
+                      (const void*)half_kernel<real, K, kModeLanczos, 0, false>,
+                      (const void*)half_kernel<real, K, kModeApply, 64, false>,
+                      (const void*)half_kernel<real, K, kModeLanczos, 64, false>,
+                      (const void*)half_kernel<real, K, kModeApply, 0, true>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
@@ -463,13 +514,13 @@ int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem) {
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
   if (c64) {
-    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 2, kModeLanczos, 0>, threads, smem);
-    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 3, kModeLanczos, 0>, threads, smem);
-    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 4, kModeLanczos, 0>, threads, smem);
+    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 2, kModeLanczos, 0, false>, threads, smem);
+    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 3, kModeLanczos, 0, false>, threads, smem);
+    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 4, kModeLanczos, 0, false>, threads, smem);
   } else {
-    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 2, kModeLanczos, 0>, threads, smem);
-    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 3, kModeLanczos, 0>, threads, smem);
-    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 4, kModeLanczos, 0>, threads, smem);
+    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 2, kModeLanczos, 0, false>, threads, smem);
+    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 3, kModeLanczos, 0, false>, threads, smem);
+    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 4, kModeLanczos, 0, false>, threads, smem);
   }
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }

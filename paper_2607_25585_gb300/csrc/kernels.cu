@@ -243,6 +243,66 @@ __device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst,
 // ---------------------------------------------------------------------------
 // the tile loop shared by every mode
 // ---------------------------------------------------------------------------
+// One element group (V values of one row) of the elementwise modes.
+template <typename real, int V, int MODE>
+__device__ __forceinline__ void elementwise_item(const InstDesc& d, const LaunchArgs& a, long long idx,
+                                                 const real* sig, const real* bsp, const real* coef, real* pacc) {
+  if (MODE == kModeEpilogue) {  // w = sigma H q_j - beta sigma' q_{j-1}; alpha and p partials
+    real ar[V], ai[V], xr[V], xi[V], wr[V], wi[V], ur[V], ui[V];
+    VecIO<real, V>::ldg(d.hq, idx, ar, ai);
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+    VecIO<real, V>::ldg(d.u, idx, ur, ui);
+    if (!a.first) {
+      real qr[V], qi[V];
+      VecIO<real, V>::ld(d.y, idx, qr, qi);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        wr[v] = fma(sig[v], ar[v], -bsp[v] * qr[v]);
+        wi[v] = fma(sig[v], ai[v], -bsp[v] * qi[v]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        wr[v] = sig[v] * ar[v];
+        wi[v] = sig[v] * ai[v];
+      }
+    }
+    VecIO<real, V>::st(d.y, idx, wr, wi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
+      pacc[v * kNumPartials + 0] += vr * wr[v] + vi * wi[v];
+      pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];
+      pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
+    }
+  } else if (MODE == kModeUpdate) {
+    real wr[V], wi[V], xr[V], xi[V];
+    VecIO<real, V>::ld(d.y, idx, wr, wi);
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      wr[v] = fma(-coef[v], xr[v], wr[v]);
+      wi[v] = fma(-coef[v], xi[v], wi[v]);
+      pacc[v * kNumPartials] += wr[v] * wr[v] + wi[v] * wi[v];
+    }
+    VecIO<real, V>::st(d.y, idx, wr, wi);
+  } else if (MODE == kModeStartNorm) {
+    real xr[V], xi[V];
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) pacc[v * kNumPartials] += xr[v] * xr[v] + xi[v] * xi[v];
+  } else if (MODE == kModeScale) {
+    real xr[V], xi[V];
+    VecIO<real, V>::ld(d.x, idx, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xr[v] *= coef[v];
+      xi[v] *= coef[v];
+    }
+    VecIO<real, V>::st(d.y, idx, xr, xi);
+  }
+}
+
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -302,6 +362,20 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
     real pacc[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) pacc[k] = 0;
+    constexpr bool kElementwise =
+        MODE == kModeEpilogue || MODE == kModeUpdate || MODE == kModeStartNorm || MODE == kModeScale;
+    if (kElementwise) {
+      // element e = row * R + col: linear over the tile; blockDim * V is a
+      // multiple of R, so each thread keeps its vector chunk
+      const long long e_end = min(row0 + a.rows_per_tile, d.dim) * a.R;
+      const long long step = (long long)blockDim.x * V;
+      long long e = row0 * a.R + (long long)threadIdx.x * V;
+      for (; e + step < e_end; e += 2 * step) {
+        elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
+        elementwise_item<real, V, MODE>(d, a, e + step, sig, bsp, coef, pacc);
+      }
+      if (e < e_end) elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
+    } else {
     const int items = a.rows_per_tile * C;
     for (int item = threadIdx.x; item < items; item += blockDim.x) {
       const long long row = row0 + item / C;
@@ -381,6 +455,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
         }
         VecIO<real, V>::st(d.y, idx, ar, ai);
       }
+    }
     }
     if (kPartials) {
 #pragma unroll

@@ -168,7 +168,7 @@ def test_ftlm_autotune_same_answer():
         assert rel(a[k], b[k], 1e-6, T >= 0.1) < 1e-10
 
 
-@pytest.mark.parametrize("shape", [(0, 1, 2), (2, 4, 1), (3, 8, 2), (4, 2, 4)])
+@pytest.mark.parametrize("shape", [(0, 1, 2), (2, 4, 1), (3, 8, 2), (4, 2, 4), (3, 8, 2, 1), (4, 8, 4, 1)])
 def test_ftlm_every_kernel_variant(shape):
     """The spin-1/2 register-cube kernel (cube_bits 2..4, vector groups,
     tile sizes) and the general kernel give the oracle's FTLM."""
