@@ -192,14 +192,15 @@ def run_ours(args):
         achieved = flops_sv * d * R / (hv_per_launch_ms / 1e3) / 1e12
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
         fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        traffic = None
-        tf = os.path.join(ROOT, "profiles", "traffic_lattice4x5.json")
-        if os.path.exists(tf):
-            try:
-                traffic = json.load(open(tf)).get("bytes_per_launch")
-            except Exception:
-                traffic = None
+        shp = results["shape"]
+        if shp["cube_bits"] > 0:
+            kname = (f"half_kernel<float,{shp['cube_bits']},Apply,{64 if R == 64 else 0},"
+                     f"{'multi' if shp['passes'] > 1 else 'single'}> (spin-1/2 register-cube gather)")
+        else:
+            kname = "rows_kernel<float,2,Lanczos> (general gather with the fused step)"
+        traffic = measured_traffic(shp)
         plain = None if args.no_plain else plain_fp64(F, s, T, spec, stream, args)
+        extra = None if args.no_extra else extra_workloads(F, T, stream, args)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -209,7 +210,7 @@ def run_ours(args):
                        "d": d, "R": R, "M": M, "global_batch_vectors": R * ws, "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (three 512 MB vector blocks)"},
             "hbm_roof_frac": value / ws * 32 / (hbm * 1e9),
-            "roofline": {"bound": "alu", "kernel": "rows_kernel<float,2,Lanczos> (fused H.v step)",
+            "roofline": {"bound": "alu", "kernel": kname,
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": traffic, "algorithmic_flops_per_sv": flops_sv,
                          "hv_ms_per_launch": hv_per_launch_ms, "launch_shape": results["shape"],
@@ -217,6 +218,7 @@ def run_ours(args):
             "hbm": {"bytes_per_sv": 32, "peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                     "frac": value / ws * 32 / (hbm * 1e9)},
             "plain_fp64": plain,
+            "other_workloads": extra,
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
         }
         if plain and plain.get("value"):
@@ -227,6 +229,24 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return line
+
+
+def measured_traffic(shape):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture, or None when the kernel source or its launch shape has changed
+    since the counters were taken."""
+    import hashlib
+    tf = os.path.join(ROOT, "profiles", "traffic_lattice4x5.json")
+    try:
+        rec = json.load(open(tf))
+        src = open(os.path.join(ROOT, rec["source_file"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        if any(rec["shape"][k] != shape.get(k) for k in rec["shape"]):
+            return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
 
 
 def plain_fp64(F, s, T, spec, stream, args):
@@ -248,6 +268,48 @@ def plain_fp64(F, s, T, spec, stream, args):
     ms = ev0.elapsed_time(ev1)
     return {"value": d * M * chains / (ms / 1e3), "unit": UNIT, "chains": chains, "M": M,
             "sample": f"{chains} complex128 chains (R=1) x {M} steps on the same system"}
+
+
+def extra_workloads(F, T, stream, args):
+    """Bounded measurements of the other workloads (reported beside the
+    headline, not part of it): the uneven-size batch of 24 s = 1 chains in
+    one graph (one full run), and the N = 26 ladder (a run of --ladder-steps
+    Lanczos steps)."""
+    import torch
+    out = {}
+    spec = W.WORKLOADS["chains_s1_x24"]
+    systems = [F.System.from_dict(w) for w in spec["system"]()]
+    R, M = spec["R"], spec["M"]
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True)
+    F.run_batch(systems, autotune=True, **kw)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = F.run_batch(systems, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sv = sum(s.dim for s in systems) * R * M
+    out["chains_s1_x24"] = {"value": sv / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R,
+                            "instances": len(systems), "hv_ms_per_launch": res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
+                            "launch_shape": res[0]["shape"], "note": "one graph for all 24 instances; general kernel"}
+    for s in systems:
+        s.close()
+    spec = W.WORKLOADS["ladder2x13"]
+    s = F.System.from_dict(spec["system"]())
+    R, M = spec["R"], args.ladder_steps
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True)
+    F.run(s, autotune=True, **kw)
+    e0.record(stream)
+    res = F.run(s, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["ladder2x13"] = {"value": s.dim * R * M / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R,
+                         "hv_ms_per_launch": res["hv_ms"] / max(1, res["hv_launches"]), "launch_shape": res["shape"],
+                         "note": f"sample of {M} Lanczos steps (the workload runs 300)"}
+    s.close()
+    return out
 
 
 def cpu_baseline(args, steps=None):
@@ -340,6 +402,8 @@ def main():
     ap.add_argument("--plain-chains", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch and ladder measurements")
+    ap.add_argument("--ladder-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--hv-only", type=int, default=0, help="time N launches of the H.v kernel alone")
     ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] instead of autotuning")
