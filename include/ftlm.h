@@ -270,7 +270,8 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
  *                 1..min(nvec, 256).
  *  tile_cubes     register-cube kernel: cubes per thread slot in a row tile, 1..64.
  *  multipass      register-cube kernel: 0 = one launch whose cube is the low
- *                 cube_bits bits; 1 = ceil(n / cube_bits) launches whose cubes
+ *                 cube_bits bits; 2 = the same with the register budget of
+ *                 three resident CTAs per SM; 1 = ceil(n / cube_bits) launches whose cubes
  *                 cover all bits, so every pair is a cube or cube-neighbour
  *                 pair of one launch (fewer gathered loads, the output is
  *                 re-read by every launch after the first).

@@ -148,6 +148,7 @@ InstDesc base_desc(const ftlm_system* s, int c64) {
 struct HalfPlan {
   bool on = false;
   int real_pm = 0;
+  int min_blocks = 2;
   int passes = 1;  // > 1: one launch per pass, cubes covering all bits
   int K = 3, Rg = 1, threads = 256, rows_per_tile = 0, grid = 0, nvg = 0, tiles_per_vg = 0;
   size_t smem = 0;
@@ -171,13 +172,15 @@ int largest_divisor_at_most(int R, int cap) {
 
 // Spin-1/2 register-cube launch: K cube bits, Rg vectors per group, tile of
 // rows_factor cubes per slot.
-bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_factor, bool multipass, HalfPlan& h) {
+bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_factor, bool multipass, HalfPlan& h,
+               int min_blocks = 2) {
   const HostSystem& hs = s->hs;
   if (!hs.all_half || hs.n < K + 2 || K < 2 || K > 4 || Rg < 1 || Rg > R) return false;
   h = HalfPlan();
   h.K = K;
   h.Rg = Rg;
   h.passes = multipass ? (hs.n + K - 1) / K : 1;
+  h.min_blocks = multipass ? 1 : (min_blocks > 2 ? 3 : 2);
   h.real_pm = hs.real_pm ? 1 : 0;
   const int slots = std::max(1, 256 / Rg);
   h.threads = slots * Rg;
@@ -192,7 +195,7 @@ bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_fac
   h.smem = half_smem_bytes(hs.n, K, h.rows_per_tile, h.threads);
   if (h.smem > 200 * 1024) return false;
   if (prepare_half_kernels(std::max<size_t>(h.smem, 48 * 1024)) != 0) return false;
-  const int per_sm = half_max_ctas_per_sm(K, c64, h.threads, h.smem);
+  const int per_sm = half_max_ctas_per_sm(K, c64, h.threads, h.smem, h.min_blocks, h.passes > 1, R);
   h.grid = (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)std::max(1, device_sm_count()) * per_sm));
   h.on = true;
   return true;
@@ -241,7 +244,8 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   pl.base = a;
   pl.half.on = false;
   if (sys.size() == 1 && pl.sh.half_K > 0)
-    make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.sh.half_multipass != 0, pl.half);
+    make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.sh.half_multipass != 0, pl.half,
+              pl.sh.half_min_blocks);
   else if (sys.size() == 1 && !force && !pl.sh.explicit_general && sys[0]->hs.all_half)
     make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 16), 4, false, pl.half);
   return FTLM_OK;
@@ -258,6 +262,7 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.tiles_per_vg = pl.half.tiles_per_vg;
     a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
     a.real_pm = pl.half.real_pm;
+    a.min_blocks = pl.half.min_blocks;
     const int K = pl.half.K;
     const int n = pl.base.max_n;
     if (pl.half.passes == 1) {
@@ -674,14 +679,17 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
     for (int mp : {0, 1})
       for (int K : {3, 4})
         for (int rg : rgs)
-          for (int f : {1, 4}) {  // cubes per thread slot in a row tile
-            Shape sh = default_shape(R, c64);
-            sh.half_K = K;
-            sh.Rg = rg;
-            sh.half_rows = f;
-            sh.half_multipass = mp;
-            if (s->hs.n >= K + 2) cands.push_back(sh);
-          }
+          for (int f : {1, 4})  // cubes per thread slot in a row tile
+            for (int mb : {2, 3}) {
+              if (mp && mb > 1) continue;
+              Shape sh = default_shape(R, c64);
+              sh.half_K = K;
+              sh.Rg = rg;
+              sh.half_rows = f;
+              sh.half_multipass = mp;
+              sh.half_min_blocks = mb;
+              if (s->hs.n >= K + 2) cands.push_back(sh);
+            }
   } else {
     for (int thr : {128, 256})
       for (int f : {1, 4}) cands.push_back(shape_for(R, c64, thr, f));
@@ -1017,6 +1025,8 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     sh.Rg = group_vectors;
     sh.half_rows = tile_cubes;
     sh.half_multipass = multipass ? 1 : 0;
+    sh.half_min_blocks = multipass >= 2 ? 3 : 2;  // multipass == 2: single pass, 3-CTA register budget
+    if (multipass >= 2) sh.half_multipass = 0;
   }
   std::lock_guard<std::mutex> lk(g_mu);
   g_shapes[key] = sh;

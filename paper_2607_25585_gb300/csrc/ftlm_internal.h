@@ -135,6 +135,7 @@ struct LaunchArgs {
   int later_lo = 0;     // bits >= later_lo outside the cube: partners of the mixed pairs
   int first_pass = 1;   // 1: diagonal, and the output is written; 0: the output is accumulated
   int single_pass = 1;  // 1: the single-pass form (cube on the low K bits, all flags implied)
+  int min_blocks = 2;   // register budget of the spin-1/2 kernel: 2 or 3 resident CTAs per SM
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -146,6 +147,7 @@ struct Shape {
   int Rg = 0;           // spin-1/2 kernel: vectors per group
   int half_rows = 2;    // spin-1/2 kernel: cubes per thread slot in a row tile
   int half_multipass = 0;  // spin-1/2 kernel: 1 = ceil(N/K) passes whose cubes cover all bits
+  int half_min_blocks = 2; // spin-1/2 kernel: register budget of 2 or 3 CTAs per SM
   bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
 };
 
@@ -166,7 +168,7 @@ int device_sm_count();
 int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size_t smem, void* stream);
 size_t half_smem_bytes(int n, int K, int rows_per_tile, int threads);
 int prepare_half_kernels(size_t smem);
-int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem);
+int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem, int min_blocks, bool multipass, int R);
 
 // Host tridiagonal eigensolver + sums (tridiag.cpp).
 ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,

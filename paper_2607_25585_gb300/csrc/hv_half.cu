@@ -136,8 +136,9 @@ __device__ __forceinline__ typename Cx<real>::v2 ldx(const void* x, long long id
 // MP: one pass of the multi-pass form (cube position and pass flags from the
 // launch arguments); otherwise the single-pass form with the cube on the low
 // K bits, every choice known at compile time.
-template <typename real, int K, int MODE, int RS, bool MP>
-__global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ LaunchArgs a) {
+// MINB: resident CTAs per SM the register allocator must allow (2 or 3).
+template <typename real, int K, int MODE, int RS, bool MP, int MINB>
+__global__ void __launch_bounds__(256, MINB) half_kernel(const __grid_constant__ LaunchArgs a) {
   using v2 = typename Cx<real>::v2;
   constexpr int NR = 1 << K;
   constexpr bool kPartials = MODE == kModeLanczos;
@@ -449,23 +450,26 @@ __global__ void __launch_bounds__(256) half_kernel(const __grid_constant__ Launc
 }
 
 // ---------------------------------------------------------------------------
-template <typename real, int K, int RS>
+template <typename real, int K, int RS, int MINB>
 static int launch_krs(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
-  if (a.mode == kModeApply) half_kernel<real, K, kModeApply, RS, false><<<grid, threads, smem, st>>>(a);
-  else if (a.mode == kModeLanczos) half_kernel<real, K, kModeLanczos, RS, false><<<grid, threads, smem, st>>>(a);
-  else return (int)cudaErrorInvalidValue;
+  if (a.mode != kModeApply) return (int)cudaErrorInvalidValue;  // the Lanczos step runs the gather alone
+  half_kernel<real, K, kModeApply, RS, false, MINB><<<grid, threads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
 template <typename real, int K>
 static int launch_k(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
-  if (!a.single_pass) {  // one pass of the multi-pass form (H.v only)
-    if (a.mode != kModeApply) return (int)cudaErrorInvalidValue;
-    half_kernel<real, K, kModeApply, 0, true><<<grid, threads, smem, st>>>(a);
+  if (a.mode != kModeApply) return (int)cudaErrorInvalidValue;
+  if (!a.single_pass) {  // one pass of the multi-pass form
+    half_kernel<real, K, kModeApply, 0, true, 1><<<grid, threads, smem, st>>>(a);
     return (int)cudaGetLastError();
   }
-  if (a.R == 64) return launch_krs<real, K, 64>(a, grid, threads, smem, st);
-  return launch_krs<real, K, 0>(a, grid, threads, smem, st);
+  if (a.min_blocks > 2) {
+    if (a.R == 64) return launch_krs<real, K, 64, 3>(a, grid, threads, smem, st);
+    return launch_krs<real, K, 0, 3>(a, grid, threads, smem, st);
+  }
+  if (a.R == 64) return launch_krs<real, K, 64, 2>(a, grid, threads, smem, st);
+  return launch_krs<real, K, 0, 2>(a, grid, threads, smem, st);
 }
 
 int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size_t smem, void* stream) {
@@ -488,11 +492,11 @@ int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size
 
 template <typename real, int K>
 static int allow_half(int bytes) {
-  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply, 0, false>,
-                      (const void*)half_kernel<real, K, kModeLanczos, 0, false>,
-                      (const void*)half_kernel<real, K, kModeApply, 64, false>,
-                      (const void*)half_kernel<real, K, kModeLanczos, 64, false>,
-                      (const void*)half_kernel<real, K, kModeApply, 0, true>};
+  const void* ks[] = {(const void*)half_kernel<real, K, kModeApply, 0, false, 2>,
+                      (const void*)half_kernel<real, K, kModeApply, 64, false, 2>,
+                      (const void*)half_kernel<real, K, kModeApply, 0, false, 3>,
+                      (const void*)half_kernel<real, K, kModeApply, 64, false, 3>,
+                      (const void*)half_kernel<real, K, kModeApply, 0, true, 1>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
@@ -510,19 +514,31 @@ int prepare_half_kernels(size_t smem) {
   return e;
 }
 
-int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem) {
+// Occupancy of the instantiation launch_k would pick for these arguments.
+template <typename real, int K>
+static int occ(int threads, size_t smem, int min_blocks, bool mp, int R) {
   int nb = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  if (c64) {
-    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 2, kModeLanczos, 0, false>, threads, smem);
-    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 3, kModeLanczos, 0, false>, threads, smem);
-    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<float, 4, kModeLanczos, 0, false>, threads, smem);
-  } else {
-    if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 2, kModeLanczos, 0, false>, threads, smem);
-    if (K == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 3, kModeLanczos, 0, false>, threads, smem);
-    if (K == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<double, 4, kModeLanczos, 0, false>, threads, smem);
-  }
+  cudaError_t e;
+  if (mp) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<real, K, kModeApply, 0, true, 1>, threads, smem);
+  else if (min_blocks > 2 && R == 64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<real, K, kModeApply, 64, false, 3>, threads, smem);
+  else if (min_blocks > 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<real, K, kModeApply, 0, false, 3>, threads, smem);
+  else if (R == 64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<real, K, kModeApply, 64, false, 2>, threads, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, half_kernel<real, K, kModeApply, 0, false, 2>, threads, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem, int min_blocks, bool multipass, int R) {
+  if (c64) {
+    if (K == 2) return occ<float, 2>(threads, smem, min_blocks, multipass, R);
+    if (K == 3) return occ<float, 3>(threads, smem, min_blocks, multipass, R);
+    return occ<float, 4>(threads, smem, min_blocks, multipass, R);
+  }
+  if (K == 2) return occ<double, 2>(threads, smem, min_blocks, multipass, R);
+  if (K == 3) return occ<double, 3>(threads, smem, min_blocks, multipass, R);
+  return occ<double, 4>(threads, smem, min_blocks, multipass, R);
 }
 
 }  // namespace ftlm
