@@ -369,8 +369,10 @@ def run_hv_only(args):
     import paper_2607_25585_gb300 as F
 
     F.build()
-    spec = W.WORKLOADS[WORKLOAD]
+    spec = W.WORKLOADS[args.hv_workload]
     w = spec["system"]()
+    if isinstance(w, list):  # a batch: the largest instance
+        w = max(w, key=lambda v: int(np.prod(v["two_s"].astype(np.int64) + 1)))
     s = F.System.from_dict(w)
     d, R = s.dim, spec["R"]
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -387,7 +389,7 @@ def run_hv_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.hv_only
-    return {"mode": "hv_only", "workload": WORKLOAD, "d": d, "R": R, "launches": args.hv_only,
+    return {"mode": "hv_only", "workload": args.hv_workload, "d": d, "R": R, "launches": args.hv_only,
             "ms_per_launch": ms, "states_vectors_per_s": d * R / (ms / 1e3)}
 
 
@@ -406,6 +408,8 @@ def main():
     ap.add_argument("--ladder-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--hv-only", type=int, default=0, help="time N launches of the H.v kernel alone")
+    ap.add_argument("--hv-workload", default=WORKLOAD, choices=sorted(W.WORKLOADS),
+                    help="workload of --hv-only (a batch uses its largest instance)")
     ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] instead of autotuning")
     args = ap.parse_args()
     if args.hv_only:

@@ -280,7 +280,12 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     }
     return 0;
   }
-  return launch_rows(a, pl.c64, pl.grid, pl.sh.threads, pl.smem, st);
+  // the streaming modes need far fewer CTAs than the gathers to saturate HBM,
+  // and fewer CTAs means fewer partial sums for the last CTA to add up
+  const bool streaming = a.mode == kModeEpilogue || a.mode == kModeUpdate || a.mode == kModeStartNorm ||
+                         a.mode == kModeScale;
+  const int grid = streaming ? std::min(pl.grid, 2 * std::max(1, device_sm_count())) : pl.grid;
+  return launch_rows(a, pl.c64, grid, pl.sh.threads, pl.smem, st);
 }
 
 int plan_max_grid(const Plan& pl) { return std::max(pl.grid, pl.half.on ? pl.half.grid : 0); }

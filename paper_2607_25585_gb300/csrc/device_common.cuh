@@ -91,63 +91,60 @@ __device__ __forceinline__ int find_instance(const int* tile_start, int n_inst, 
 }
 
 
-// Last CTA: total[inst][r][c] = sum over CTAs in order, a warp per (inst, r, c).
+// Last CTA: total[inst][r][c] = sum over the CTAs' partials in a fixed order
+// (four interleaved partial sums, combined in a fixed order), one thread per
+// (inst, r, c): deterministic for a given grid.
 __device__ inline double total_partial(const LaunchArgs& a, int inst, int r, int c) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  const double* base = a.partials + (size_t)inst * gridDim.x * (size_t)a.R * kNumPartials;
-  for (int b = lane; b < (int)gridDim.x; b += 32) s += base[((size_t)b * a.R + r) * kNumPartials + c];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
+  const double* base = a.partials + (size_t)inst * gridDim.x * (size_t)a.R * kNumPartials + (size_t)r * kNumPartials + c;
+  const size_t stride = (size_t)a.R * kNumPartials;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int b = 0;
+  for (; b + 4 <= (int)gridDim.x; b += 4) {
+    s0 += base[(size_t)b * stride];
+    s1 += base[(size_t)(b + 1) * stride];
+    s2 += base[(size_t)(b + 2) * stride];
+    s3 += base[(size_t)(b + 3) * stride];
+  }
+  for (; b < (int)gridDim.x; ++b) s0 += base[(size_t)b * stride];
+  return (s0 + s1) + (s2 + s3);
 }
 
 __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
   // (inst_all points at the device array, or at the inline descriptor)
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
   const int R = a.R;
-  for (int item = warp; item < a.n_inst * R; item += nwarps) {
+  for (int item = threadIdx.x; item < a.n_inst * R; item += blockDim.x) {
     const int inst = item / R, r = item % R;
     const InstDesc& d = inst_all[inst];
     const DevScalars& sc = d.sc;
     const int j = a.step;
     if (a.mode == kModeLanczos || a.mode == kModeEpilogue) {
-      const double al = total_partial(a, inst, r, 0);
-      const double pr = total_partial(a, inst, r, 1);
-      const double pi = total_partial(a, inst, r, 2);
-      if (lane == 0) {
-        sc.alpha[(size_t)j * R + r] = al;
-        sc.p[((size_t)j * R + r) * 2] = pr;
-        sc.p[((size_t)j * R + r) * 2 + 1] = pi;
-      }
+      sc.alpha[(size_t)j * R + r] = total_partial(a, inst, r, 0);
+      sc.p[((size_t)j * R + r) * 2] = total_partial(a, inst, r, 1);
+      sc.p[((size_t)j * R + r) * 2 + 1] = total_partial(a, inst, r, 2);
     } else if (a.mode == kModeUpdate) {
       const double nrm2 = total_partial(a, inst, r, 0);
-      if (lane == 0) {
-        const double bnew = sqrt(fmax(nrm2, 0.0));
-        const double al = sc.alpha[(size_t)j * R + r];
-        const double bold = j > 0 ? sc.beta[(size_t)(j - 1) * R + r] : 0.0;
-        double scl = fmax(sc.scale[r], fmax(fabs(al), bold));
-        sc.scale[r] = scl;
-        sc.beta[(size_t)j * R + r] = bnew;
-        double sig = 0.0;
-        if (sc.active[r]) {
-          if (j < d.M - 1 && (!(bnew > d.tol * scl) || !isfinite(bnew) || !isfinite(al))) {
-            sc.active[r] = 0;
-            sc.meff[r] = j + 1;
-          } else {
-            sig = bnew > 0.0 ? 1.0 / bnew : 0.0;
-          }
+      const double bnew = sqrt(fmax(nrm2, 0.0));
+      const double al = sc.alpha[(size_t)j * R + r];
+      const double bold = j > 0 ? sc.beta[(size_t)(j - 1) * R + r] : 0.0;
+      double scl = fmax(sc.scale[r], fmax(fabs(al), bold));
+      sc.scale[r] = scl;
+      sc.beta[(size_t)j * R + r] = bnew;
+      double sig = 0.0;
+      if (sc.active[r]) {
+        if (j < d.M - 1 && (!(bnew > d.tol * scl) || !isfinite(bnew) || !isfinite(al))) {
+          sc.active[r] = 0;
+          sc.meff[r] = j + 1;
+        } else {
+          sig = bnew > 0.0 ? 1.0 / bnew : 0.0;
         }
-        sc.sigma[(size_t)(j + 1) * R + r] = sig;
       }
+      sc.sigma[(size_t)(j + 1) * R + r] = sig;
     } else if (a.mode == kModeStartNorm) {
-      const double nrm2 = total_partial(a, inst, r, 0);
-      if (lane == 0) {
-        const double nrm = sqrt(fmax(nrm2, 0.0));
-        sc.sigma[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        sc.scale[r] = 0.0;
-        sc.active[r] = nrm > 0.0 ? 1 : 0;
-        sc.meff[r] = nrm > 0.0 ? d.M : 0;
-      }
+      const double nrm = sqrt(fmax(total_partial(a, inst, r, 0), 0.0));
+      sc.sigma[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      sc.scale[r] = 0.0;
+      sc.active[r] = nrm > 0.0 ? 1 : 0;
+      sc.meff[r] = nrm > 0.0 ? d.M : 0;
     }
   }
 }

@@ -637,9 +637,12 @@ int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream) {
 }
 
 int device_sm_count() {
+  static int cached[64] = {};  // per device ordinal; queried once, outside any stream capture
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64) cached[dev] = n;
   return n;
 }
 
