@@ -193,7 +193,10 @@ def run_ours(args):
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
         fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         shp = results["shape"]
-        if shp["cube_bits"] > 0:
+        if shp.get("vector_major"):
+            kname = (f"vm_kernel<float,{shp['cube_bits']},{'multi' if shp['passes'] > 1 else 'single'}> "
+                     f"(vector-major spin-1/2 gather{', %d passes' % shp['passes'] if shp['passes'] > 1 else ''})")
+        elif shp["cube_bits"] > 0:
             kname = (f"half_kernel<float,{shp['cube_bits']},Apply,{64 if R == 64 else 0},"
                      f"{'multi' if shp['passes'] > 1 else 'single'}> (spin-1/2 register-cube gather)")
         else:

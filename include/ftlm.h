@@ -219,6 +219,7 @@ typedef struct {
   int tile_rows;          /* rows per tile */
   int grid;               /* CTAs per H.v launch */
   int threads;            /* threads per CTA */
+  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..5) */
 } ftlm_result;
 
 /*
@@ -275,6 +276,18 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
  *                 cover all bits, so every pair is a cube or cube-neighbour
  *                 pair of one launch (fewer gathered loads, the output is
  *                 re-read by every launch after the first).
+ *                 3 = (ftlm_run only; cube_bits 3 or 4, n_sites >= 5 + cube_bits)
+ *                 vector-major Lanczos block: each of the R vectors is
+ *                 contiguous, the 32 lanes of a warp own 32 consecutive rows
+ *                 and each thread a cube along bits [5, 5 + cube_bits), so a
+ *                 vector's gathered slice is d elements; 4 = the same with the
+ *                 three-CTA register budget; 5 = vector-major in
+ *                 ceil((n - 5) / cube_bits) launches whose cubes cover bits
+ *                 [5, n), so that every pair is a cube, mixed or lane-lane
+ *                 pair of one launch.  group_vectors is ignored and
+ *                 tile_cubes counts slabs of 2^(5 + cube_bits) rows per warp.
+ *                 ftlm_apply_h on row-major blocks uses the row-major
+ *                 register-cube kernel for these shapes.
  * Host-only; returns FTLM_ERR_UNSUPPORTED for cube_bits > 0 on other spins.
  */
 ftlm_status ftlm_tune_shape(const ftlm_system* sys, int nvec, ftlm_dtype dtype, int cube_bits, int group_vectors,

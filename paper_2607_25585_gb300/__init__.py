@@ -58,7 +58,7 @@ class Result(ctypes.Structure):
         ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
         ("cube_bits", ctypes.c_int), ("passes", ctypes.c_int), ("group_vectors", ctypes.c_int),
         ("tile_rows", ctypes.c_int),
-        ("grid", ctypes.c_int), ("threads", ctypes.c_int),
+        ("grid", ctypes.c_int), ("threads", ctypes.c_int), ("vector_major", ctypes.c_int),
     ]
 
 
@@ -255,7 +255,7 @@ def _finish(r, out):
                kernel_launches=r.kernel_launches, h2d_bytes=int(r.h2d_bytes), d2h_bytes=int(r.d2h_bytes),
                shape={"cube_bits": r.cube_bits, "passes": r.passes, "group_vectors": r.group_vectors,
                       "tile_rows": r.tile_rows,
-                      "grid": r.grid, "threads": r.threads})
+                      "grid": r.grid, "threads": r.threads, "vector_major": r.vector_major})
     return out
 
 

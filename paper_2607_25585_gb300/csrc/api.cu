@@ -147,11 +147,13 @@ InstDesc base_desc(const ftlm_system* s, int c64) {
 
 struct HalfPlan {
   bool on = false;
+  bool vm = false;  // vector-major kernel: R instances of one vector each (nvg = R, Rg = 1)
   int real_pm = 0;
   int min_blocks = 2;
   int passes = 1;  // > 1: one launch per pass, cubes covering all bits
   int K = 3, Rg = 1, threads = 256, rows_per_tile = 0, grid = 0, nvg = 0, tiles_per_vg = 0;
   size_t smem = 0;
+  int stream_rows = 0, stream_tiles_per_vg = 0, stream_grid = 0;  // vector-major streaming launches
 };
 
 struct Plan {
@@ -201,22 +203,45 @@ bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_fac
   return true;
 }
 
-ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan& pl, const Shape* force = nullptr) {
-  pl.c64 = c64;
-  pl.R = R;
+// Vector-major spin-1/2 launch: K cube bits above the 5 lane bits, tiles of
+// 8 warps x rows_factor slabs of 2^(5+K) rows, R tiles ranges (one per vector).
+bool make_vm(const ftlm_system* s, int R, int c64, int K, int rows_factor, int min_blocks, bool multipass,
+             HalfPlan& h) {
+  const HostSystem& hs = s->hs;
+  if (!hs.all_half || K < 3 || K > 4 || hs.n < kVmLaneBits + K || rows_factor < 1) return false;
+  h = HalfPlan();
+  h.vm = true;
+  h.K = K;
+  h.Rg = 1;
+  h.passes = multipass ? (hs.n - kVmLaneBits + K - 1) / K : 1;  // cubes cover bits [5, n)
+  h.min_blocks = h.passes > 1 ? 2 : (min_blocks > 2 ? 3 : 2);
+  h.real_pm = hs.real_pm ? 1 : 0;
+  h.threads = 256;
+  const long long slab = 1ll << (kVmLaneBits + K);
+  long long rows = (long long)(h.threads / 32) * slab * rows_factor;
+  rows = std::min<long long>(rows, (long long)hs.dim);  // dim and rows are powers of two >= slab
+  h.rows_per_tile = (int)rows;
+  h.nvg = R;
+  h.tiles_per_vg = (int)((long long)hs.dim / rows);
+  const long long ntiles = (long long)h.tiles_per_vg * R;
+  if (ntiles > (1ll << 30)) return false;
+  h.smem = vm_smem_bytes(hs.n, K, h.threads);
+  if (h.smem > 200 * 1024) return false;
+  if (prepare_vm_kernels(std::max<size_t>(h.smem, 48 * 1024)) != 0) return false;
+  const int per_sm = vm_max_ctas_per_sm(K, h.min_blocks, c64, h.threads, h.smem, h.passes > 1);
+  const long long sms = std::max(1, device_sm_count());
+  h.grid = (int)std::max<long long>(1, std::min<long long>(ntiles, sms * per_sm));
+  h.stream_rows = (int)std::min<long long>(16384, (long long)hs.dim);
+  h.stream_tiles_per_vg = (int)((long long)hs.dim / h.stream_rows);
+  h.stream_grid = (int)std::max<long long>(1, std::min<long long>((long long)h.stream_tiles_per_vg * R, sms * 4));
+  h.on = true;
+  return true;
+}
+
+// General row-kernel launch over the instances `sys` (R vectors each).
+ftlm_status make_general(const std::vector<ftlm_system*>& sys, int R, int c64, Plan& pl) {
   pl.V = vchunk(c64, R);
   pl.C = R / pl.V;
-  const ftlm_system* big = sys[0];
-  for (auto* s : sys)
-    if (s->hs.dim > big->hs.dim) big = s;
-  if (force) {
-    pl.sh = *force;
-  } else {
-    ShapeKey key{big->hs.n, big->hs.qmax, R, c64, (long long)big->hs.dim};
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_shapes.find(key);
-    pl.sh = it != g_shapes.end() ? it->second : default_shape(R, c64);
-  }
   LaunchArgs a;
   a.R = R;
   a.C = pl.C;
@@ -242,11 +267,59 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   const int sms = std::max(1, device_sm_count());
   pl.grid = std::max(1, std::min(a.ntiles, sms * per_sm));
   pl.base = a;
+  return FTLM_OK;
+}
+
+// allow_vm: the caller keeps its Lanczos block vector-major (ftlm_run); for
+// row-major blocks a vector-major shape falls back to the row-major cube kernel.
+ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan& pl, const Shape* force = nullptr,
+                      bool allow_vm = false) {
+  pl.c64 = c64;
+  pl.R = R;
+  const ftlm_system* big = sys[0];
+  for (auto* s : sys)
+    if (s->hs.dim > big->hs.dim) big = s;
+  if (force) {
+    pl.sh = *force;
+  } else {
+    ShapeKey key{big->hs.n, big->hs.qmax, R, c64, (long long)big->hs.dim};
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_shapes.find(key);
+    pl.sh = it != g_shapes.end() ? it->second : default_shape(R, c64);
+  }
   pl.half.on = false;
-  if (sys.size() == 1 && pl.sh.half_K > 0)
+  if (sys.size() == 1 && pl.sh.half_K > 0 && pl.sh.half_vm && allow_vm &&
+      make_vm(sys[0], R, c64, pl.sh.half_K, pl.sh.half_rows, pl.sh.half_min_blocks, pl.sh.half_multipass != 0,
+              pl.half)) {
+    // the streaming modes see R one-vector instances of the same system
+    const Shape keep = pl.sh;
+    pl.sh = default_shape(1, c64);
+    ftlm_status gs = make_general(std::vector<ftlm_system*>(R, sys[0]), 1, c64, pl);
+    pl.sh.half_K = keep.half_K;
+    pl.sh.half_vm = 1;
+    return gs;
+  }
+  if (sys.size() == 1 && allow_vm && !force && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
+    // default for runs on spin-1/2 systems: the vector-major single-pass gather
+    const int K = c64 ? 4 : 3;  // complex128 cubes of 16 rows spill at the 2-CTA register budget
+    Shape vm = pl.sh;
+    vm.half_K = K;
+    vm.half_rows = 2;
+    vm.half_vm = 1;
+    if (make_vm(sys[0], R, c64, K, 2, 2, false, pl.half)) {
+      pl.sh = default_shape(1, c64);
+      ftlm_status gs = make_general(std::vector<ftlm_system*>(R, sys[0]), 1, c64, pl);
+      pl.sh.half_K = K;
+      pl.sh.half_vm = 1;
+      return gs;
+    }
+  }
+  ftlm_status gs = make_general(sys, R, c64, pl);
+  if (gs != FTLM_OK) return gs;
+  if (sys.size() == 1 && pl.sh.half_K > 0 && !pl.sh.half_vm)
     make_half(sys[0], R, c64, pl.sh.half_K, pl.sh.Rg, pl.sh.half_rows, pl.sh.half_multipass != 0, pl.half,
               pl.sh.half_min_blocks);
-  else if (sys.size() == 1 && !force && !pl.sh.explicit_general && sys[0]->hs.all_half)
+  else if (sys.size() == 1 && (!force || pl.sh.half_vm) && !pl.sh.explicit_general && sys[0]->hs.all_half)
     make_half(sys[0], R, c64, 3, largest_divisor_at_most(R, 16), 4, false, pl.half);
   return FTLM_OK;
 }
@@ -254,7 +327,41 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
 // Launches one mode of the plan: the spin-1/2 kernel for H.v modes when the
 // plan has it, the general row kernel otherwise.
 int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
-  const bool half = pl.half.on && (a.mode == kModeApply || (a.mode == kModeLanczos && pl.half.passes == 1));
+  if (pl.half.on && pl.half.vm && (a.mode == kModeStep || a.mode == kModeStartNorm)) {
+    a.rows_per_tile = pl.half.stream_rows;
+    a.tiles_per_vg = pl.half.stream_tiles_per_vg;
+    a.n_inst = pl.half.nvg;
+    a.ntiles = pl.half.stream_tiles_per_vg * pl.half.nvg;
+    a.inline_one = 0;
+    return launch_vm_stream(a, pl.c64, pl.half.stream_grid, st);
+  }
+  if (pl.half.on && pl.half.vm && a.mode == kModeApply) {  // a.inst: R one-vector instances
+    a.rows_per_tile = pl.half.rows_per_tile;
+    a.tiles_per_vg = pl.half.tiles_per_vg;
+    a.nvg = pl.half.nvg;
+    a.n_inst = pl.half.nvg;
+    a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
+    a.real_pm = pl.half.real_pm;
+    a.min_blocks = pl.half.min_blocks;
+    a.inline_one = 0;
+    if (pl.half.passes == 1) {
+      a.single_pass = 1;
+      return launch_vm(a, pl.half.K, pl.half.min_blocks, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+    }
+    const int K = pl.half.K, n = pl.base.max_n, ga = a.gather_alpha;
+    for (int p = 0; p < pl.half.passes; ++p) {  // cubes [min(5 + pK, n - K), +K) cover bits [5, n)
+      a.cube_lo = std::min(kVmLaneBits + p * K, n - K);
+      a.new_lo = kVmLaneBits + p * K;
+      a.first_pass = p == 0;
+      a.single_pass = 0;
+      a.gather_alpha = p == pl.half.passes - 1 ? ga : 0;  // alpha from the complete H q_j
+      const int e = launch_vm(a, K, 2, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+      if (e) return e;
+    }
+    return 0;
+  }
+  const bool half = pl.half.on && !pl.half.vm &&
+                    (a.mode == kModeApply || (a.mode == kModeLanczos && pl.half.passes == 1));
   if (half) {
     a.rows_per_tile = pl.half.rows_per_tile;
     a.Rg = pl.half.Rg;
@@ -283,12 +390,14 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
   // the streaming modes need far fewer CTAs than the gathers to saturate HBM,
   // and fewer CTAs means fewer partial sums for the last CTA to add up
   const bool streaming = a.mode == kModeEpilogue || a.mode == kModeUpdate || a.mode == kModeStartNorm ||
-                         a.mode == kModeScale;
+                         a.mode == kModeScale || a.mode == kModeStep;
   const int grid = streaming ? std::min(pl.grid, 2 * std::max(1, device_sm_count())) : pl.grid;
   return launch_rows(a, pl.c64, grid, pl.sh.threads, pl.smem, st);
 }
 
-int plan_max_grid(const Plan& pl) { return std::max(pl.grid, pl.half.on ? pl.half.grid : 0); }
+int plan_max_grid(const Plan& pl) {
+  return std::max(pl.grid, pl.half.on ? std::max(pl.half.grid, pl.half.stream_grid) : 0);
+}
 
 // ---- workspace ----------------------------------------------------------------
 
@@ -324,6 +433,7 @@ ftlm_status ensure_hq(ftlm_system* s, int R, int c64) {
 
 DevScalars scalars_at(void* base, int R, int M) {
   DevScalars sc;
+  sc.ss = R;
   double* b = reinterpret_cast<double*>(base);
   sc.alpha = b;
   b += (size_t)M * R;
@@ -338,6 +448,20 @@ DevScalars scalars_at(void* base, int R, int M) {
   int* ib = reinterpret_cast<int*>(b);
   sc.active = ib;
   sc.meff = ib + R;
+  return sc;
+}
+
+// The scalars of vector k alone, as a one-vector instance sees them (row
+// stride R in the shared arrays).
+DevScalars scalars_of_vector(void* base, int R, int M, int k) {
+  DevScalars sc = scalars_at(base, R, M);
+  sc.alpha += k;
+  sc.beta += k;
+  sc.p += 2 * k;
+  sc.sigma += k;
+  sc.scale += k;
+  sc.active += k;
+  sc.meff += k;
   return sc;
 }
 
@@ -392,8 +516,8 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
            (unsigned long long)p->basis_offset, p->user_start, p->time_kernels, pl.sh.threads, pl.sh.rows_per_tile,
            pl.grid, p->breakdown_tol, u[0], u[1], u[2], p->obs_dir ? 1 : 0, p->stream);
   k += buf;
-  snprintf(buf, sizeof buf, "|half%d K%d Rg%d rpt%d g%d P%d", pl.half.on ? 1 : 0, pl.half.K, pl.half.Rg,
-           pl.half.rows_per_tile, pl.half.grid, pl.half.passes);
+  snprintf(buf, sizeof buf, "|half%d vm%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
+           pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
   return k + buf;
 }
 
@@ -432,12 +556,16 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
                         cudaStream_t st) {
   const int M = p->M, R = p->R, c64 = pl.c64;
   const int n = (int)sys.size();
+  const int nd = pl.half.vm ? R : n;  // descriptors per kind: one per vector in the vector-major layout
   const InstDesc* d_even = reinterpret_cast<const InstDesc*>(ctx.desc.p);
-  const InstDesc* d_odd = d_even + n;
-  const InstDesc* d_start = d_even + 2 * n;
-  const InstDesc* d_gather_even = d_even + 3 * n;  // split steps: x = q_j, y = Hq
-  const InstDesc* d_gather_odd = d_even + 4 * n;
+  const InstDesc* d_odd = d_even + nd;
+  const InstDesc* d_start = d_even + 2 * nd;
+  const InstDesc* d_gather_even = d_even + 3 * nd;  // split steps: x = q_j, y = Hq
+  const InstDesc* d_gather_odd = d_even + 4 * nd;
   const bool split = pl.half.on;  // the spin-1/2 gather runs alone; the step epilogue streams afterwards
+  // single-pass gathers also sum Re<q_j|H q_j>, so alpha_j is known before the
+  // epilogue, which then finishes the step in one pass (no separate update)
+  const bool fused = split && (pl.half.passes == 1 || pl.half.vm);
   LaunchArgs a = pl.base;
   a.tile_start = reinterpret_cast<const int*>(ctx.tiles.p);
   a.partials = reinterpret_cast<double*>(ctx.partials.p);
@@ -447,14 +575,18 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   const bool tk = p->time_kernels != 0;
   int evi = 0;
   if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+  const int vmaj = pl.half.vm ? 1 : 0;
   for (int k = 0; k < n; ++k) {  // start block -> A
     InstDesc h = base_desc(sys[k], c64);
+    const long long dim = (long long)sys[k]->hs.dim;
     if (p->start == FTLM_START_RANDOM)
-      CKI(launch_start_random(&h, nullptr, R, p->seed, p->vec_offset, sys[k]->A.p, c64, st));
+      CKI(launch_start_random(&h, nullptr, R, p->seed, p->vec_offset, sys[k]->A.p, c64, st, vmaj));
     else if (p->start == FTLM_START_BASIS)
-      CKI(launch_start_basis((long long)sys[k]->hs.dim, R, p->basis_offset, sys[k]->A.p, c64, st));
+      CKI(launch_start_basis(dim, R, p->basis_offset, sys[k]->A.p, c64, st, vmaj));
+    else if (vmaj)
+      CKI(launch_to_vector_major(p->user_start, sys[k]->A.p, dim, R, c64, st));
     else
-      CKI(launch_copy_block(p->user_start, sys[k]->A.p, (size_t)sys[k]->hs.dim * R * (c64 ? 8 : 16), st));
+      CKI(launch_copy_block(p->user_start, sys[k]->A.p, (size_t)dim * R * (c64 ? 8 : 16), st));
     ctx.launches++;
   }
   a.inst = d_start;  // sigma_0 = 1/|q_0|, then U = sigma_0 (u.S) q_0
@@ -473,9 +605,17 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       LaunchArgs g = a;
       g.inst = (j % 2 == 0) ? d_gather_even : d_gather_odd;
       g.mode = kModeApply;
+      g.gather_alpha = fused ? 1 : 0;
       if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
       CKI(launch_plan(pl, g, st));
       if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      if (fused) {
+        a.mode = kModeStep;
+        CKI(launch_plan(pl, a, st));
+        ctx.launches += 2;
+        ctx.hv_launches++;
+        continue;
+      }
       a.mode = kModeEpilogue;
       CKI(launch_plan(pl, a, st));
       ctx.launches++;
@@ -506,40 +646,47 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
   const int c64 = pl.c64, R = p->R, M = p->M, n = (int)sys.size();
   for (auto* s : sys) c.deps.push_back(s->id);
   // descriptors: even steps (x = A, y = B), odd steps (x = B, y = A), start (x = A, y = U),
-  // and for split steps the gathers (x = A or B, y = Hq)
-  std::vector<InstDesc> h(5 * n);
-  for (int k = 0; k < n; ++k) {
-    ftlm_system* s = sys[k];
+  // and for split steps the gathers (x = A or B, y = Hq); one per system, or in the
+  // vector-major layout one per vector (pointers at vector k, scalars of vector k)
+  const int nd = pl.half.vm ? R : n;
+  std::vector<InstDesc> h(5 * nd);
+  for (int k = 0; k < nd; ++k) {
+    ftlm_system* s = sys[pl.half.vm ? 0 : k];
     InstDesc d = base_desc(s, c64);
-    d.sc = scalars_at(s->scal.p, R, M);
-    d.u = s->U.p;
+    d.sc = pl.half.vm ? scalars_of_vector(s->scal.p, R, M, k) : scalars_at(s->scal.p, R, M);
+    const size_t off = pl.half.vm ? (size_t)k * s->hs.dim * (c64 ? 8 : 16) : 0;  // bytes to vector k
+    char* A = static_cast<char*>(s->A.p) + off;
+    char* B = static_cast<char*>(s->B.p) + off;
+    char* U = static_cast<char*>(s->U.p) + off;
+    char* Hq = s->Hq.p ? static_cast<char*>(s->Hq.p) + off : nullptr;
+    d.u = U;
     d.M = M;
     d.tol = p->breakdown_tol > 0 ? p->breakdown_tol : (c64 ? 1e-6 : 1e-12);
     observable_coefs(s->hs, p->obs_dir, d.obs);  // per instance: each system has its own field direction
     InstDesc e = d, o = d, t = d;
-    e.x = s->A.p;
-    e.y = s->B.p;
-    o.x = s->B.p;
-    o.y = s->A.p;
-    t.x = s->A.p;
-    t.y = s->U.p;
-    e.hq = o.hq = s->Hq.p;
+    e.x = A;
+    e.y = B;
+    o.x = B;
+    o.y = A;
+    t.x = A;
+    t.y = U;
+    e.hq = o.hq = Hq;
     InstDesc ge = d, go = d;
-    ge.x = s->A.p;
-    ge.y = s->Hq.p;
-    go.x = s->B.p;
-    go.y = s->Hq.p;
+    ge.x = A;
+    ge.y = Hq;
+    go.x = B;
+    go.y = Hq;
     h[k] = e;
-    h[n + k] = o;
-    h[2 * n + k] = t;
-    h[3 * n + k] = ge;
-    h[4 * n + k] = go;
+    h[nd + k] = o;
+    h[2 * nd + k] = t;
+    h[3 * nd + k] = ge;
+    h[4 * nd + k] = go;
   }
   CK(c.desc.ensure(sizeof(InstDesc) * h.size()));
   CK(cudaMemcpy(c.desc.p, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice));
   CK(c.tiles.ensure(sizeof(int) * pl.tile_start.size()));
   CK(cudaMemcpy(c.tiles.p, pl.tile_start.data(), sizeof(int) * pl.tile_start.size(), cudaMemcpyHostToDevice));
-  CK(c.partials.ensure(sizeof(double) * (size_t)n * plan_max_grid(pl) * R * kNumPartials));
+  CK(c.partials.ensure(sizeof(double) * (size_t)n * plan_max_grid(pl) * R * kNumPartials));  // n_inst x R = R x 1 when vector-major
   CK(c.counter.ensure(64));
   CK(cudaMemset(c.counter.p, 0, 64));
   c.h2d = sizeof(InstDesc) * h.size() + sizeof(int) * pl.tile_start.size();
@@ -579,7 +726,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     if (w != FTLM_OK) return w;
   }
   Plan pl;
-  ftlm_status ps = make_plan(sys, R, c64, pl);
+  ftlm_status ps = make_plan(sys, R, c64, pl, nullptr, true);
   if (ps != FTLM_OK) return ps;
   if (pl.half.on) {
     ftlm_status hs_ = ensure_hq(sys[0], R, c64);
@@ -662,6 +809,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     out.tile_rows = pl.half.on ? pl.half.rows_per_tile : pl.sh.rows_per_tile;
     out.grid = pl.half.on ? pl.half.grid : pl.grid;
     out.threads = pl.half.on ? pl.half.threads : pl.sh.threads;
+    out.vector_major = pl.half.vm ? 1 : 0;
   }
   return FTLM_OK;
 }
@@ -695,13 +843,35 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
               sh.half_min_blocks = mb;
               if (s->hs.n >= K + 2) cands.push_back(sh);
             }
+    for (int mp : {0, 1})  // the vector-major gather (runs only)
+      for (int K : {3, 4})
+        for (int f : {1, 2, 4}) {
+          Shape sh = default_shape(R, c64);
+          sh.half_K = K;
+          sh.Rg = largest_divisor_at_most(R, 16);
+          sh.half_rows = f;
+          sh.half_multipass = mp;
+          sh.half_vm = 1;
+          if (s->hs.n >= kVmLaneBits + K) cands.push_back(sh);
+        }
   } else {
     for (int thr : {128, 256})
       for (int f : {1, 4}) cands.push_back(shape_for(R, c64, thr, f));
   }
   ftlm_status w = ensure_workspace(s, R, 1, c64);
   if (w != FTLM_OK) return w;
-  CK(cudaMemsetAsync(s->A.p, 0, (size_t)s->hs.dim * R * (c64 ? 8 : 16), st));
+  const size_t vbytes = (size_t)s->hs.dim * (c64 ? 8 : 16);
+  CK(cudaMemsetAsync(s->A.p, 0, vbytes * R, st));
+  DevBuf vdesc;  // the vector-major candidates: one descriptor per vector
+  {
+    std::vector<InstDesc> h(R, base_desc(s, c64));
+    for (int k = 0; k < R; ++k) {
+      h[k].x = static_cast<char*>(s->A.p) + vbytes * k;
+      h[k].y = static_cast<char*>(s->B.p) + vbytes * k;
+    }
+    CK(vdesc.ensure(sizeof(InstDesc) * R));
+    CK(cudaMemcpy(vdesc.p, h.data(), sizeof(InstDesc) * R, cudaMemcpyHostToDevice));
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -710,17 +880,21 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
   std::vector<ftlm_system*> one{s};
   for (const Shape& sh : cands) {
     Plan pl;
-    if (make_plan(one, R, c64, pl, &sh) != FTLM_OK) continue;
-    if (sh.half_K > 0 && !pl.half.on) continue;
+    if (make_plan(one, R, c64, pl, &sh, sh.half_vm != 0) != FTLM_OK) continue;
+    if (sh.half_K > 0 && (!pl.half.on || pl.half.vm != (sh.half_vm != 0))) continue;
     LaunchArgs a = pl.base;
-    a.inline_one = 1;
-    a.one = base_desc(s, c64);
-    a.one.x = s->A.p;
-    a.one.y = s->B.p;
+    if (pl.half.vm) {
+      a.inst = reinterpret_cast<const InstDesc*>(vdesc.p);
+    } else {
+      a.inline_one = 1;
+      a.one = base_desc(s, c64);
+      a.one.x = s->A.p;
+      a.one.y = s->B.p;
+    }
     a.mode = kModeApply;
-    CKI(launch_plan(pl, a, st));  // warm-up
+    for (int it = 0; it < 2; ++it) CKI(launch_plan(pl, a, st));  // warm-up
     CK(cudaEventRecord(e0, st));
-    for (int it = 0; it < 3; ++it) CKI(launch_plan(pl, a, st));
+    for (int it = 0; it < 5; ++it) CKI(launch_plan(pl, a, st));
     CK(cudaEventRecord(e1, st));
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -1023,15 +1197,18 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     if (!s->hs.all_half) return fail(FTLM_ERR_UNSUPPORTED, "register cubes need every site s = 1/2");
     if (cube_bits < 2 || cube_bits > 4 || s->hs.n < cube_bits + 2)
       return fail(FTLM_ERR_INVALID_ARG, "cube_bits must be 2..4 and at most n_sites - 2");
-    if (group_vectors < 1 || group_vectors > nvec || group_vectors > 256)
+    if (multipass < 0 || multipass > 5) return fail(FTLM_ERR_INVALID_ARG, "multipass must be in 0..5");
+    if (multipass >= 3 && (cube_bits < 3 || s->hs.n < kVmLaneBits + cube_bits))
+      return fail(FTLM_ERR_INVALID_ARG, "the vector-major kernel needs cube_bits 3..4 and n_sites >= 5 + cube_bits");
+    if (multipass < 3 && (group_vectors < 1 || group_vectors > nvec || group_vectors > 256))
       return fail(FTLM_ERR_INVALID_ARG, "group_vectors must be in 1..min(nvec, 256)");
     if (tile_cubes < 1 || tile_cubes > 64) return fail(FTLM_ERR_INVALID_ARG, "tile_cubes must be in 1..64");
     sh.half_K = cube_bits;
-    sh.Rg = group_vectors;
+    sh.Rg = multipass >= 3 ? largest_divisor_at_most(nvec, 16) : group_vectors;  // row-major fallback for apply_h
     sh.half_rows = tile_cubes;
-    sh.half_multipass = multipass ? 1 : 0;
-    sh.half_min_blocks = multipass >= 2 ? 3 : 2;  // multipass == 2: single pass, 3-CTA register budget
-    if (multipass >= 2) sh.half_multipass = 0;
+    sh.half_multipass = (multipass == 1 || multipass == 5) ? 1 : 0;
+    sh.half_min_blocks = (multipass == 2 || multipass == 4) ? 3 : 2;  // 2 and 4: 3-CTA register budget
+    sh.half_vm = multipass >= 3 ? 1 : 0;
   }
   std::lock_guard<std::mutex> lk(g_mu);
   g_shapes[key] = sh;

@@ -79,6 +79,97 @@ __device__ __forceinline__ void gather_mac(const void* x, long long nu, int R, i
   cmac<real, V>(ar, ai, cr, ci, xr, xi);
 }
 
+// One element group of the elementwise modes: V consecutive values at
+// complex index idx (V vectors of one row in the row-major block, or V rows of
+// one vector in the vector-major block); sig, bsp, coef are their scalars:
+//   Epilogue: sig = sigma_j, bsp = beta_{j-1} sigma_{j-1};
+//   Step: the same and coef = alpha_j sigma_j;  Update: coef = alpha_j sigma_j;
+//   Scale: coef = the factor.
+template <typename real, int V, int MODE>
+__device__ __forceinline__ void elementwise_item(const InstDesc& d, const LaunchArgs& a, long long idx,
+                                                 const real* sig, const real* bsp, const real* coef, real* pacc) {
+  if (MODE == kModeEpilogue) {  // w = sigma H q_j - beta sigma' q_{j-1}; alpha and p partials
+    real ar[V], ai[V], xr[V], xi[V], wr[V], wi[V], ur[V], ui[V];
+    VecIO<real, V>::ldg(d.hq, idx, ar, ai);
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+    VecIO<real, V>::ldg(d.u, idx, ur, ui);
+    if (!a.first) {
+      real qr[V], qi[V];
+      VecIO<real, V>::ld(d.y, idx, qr, qi);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        wr[v] = fma(sig[v], ar[v], -bsp[v] * qr[v]);
+        wi[v] = fma(sig[v], ai[v], -bsp[v] * qi[v]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        wr[v] = sig[v] * ar[v];
+        wi[v] = sig[v] * ai[v];
+      }
+    }
+    VecIO<real, V>::st(d.y, idx, wr, wi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
+      pacc[v * kNumPartials + 0] += vr * wr[v] + vi * wi[v];
+      pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];
+      pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
+    }
+  } else if (MODE == kModeStep) {  // w = sigma hq - bsp q_{j-1} - alpha sigma q_j; partials |w|^2, p
+    real ar[V], ai[V], xr[V], xi[V], qr[V], qi[V], ur[V], ui[V];
+    VecIO<real, V>::ldg(d.hq, idx, ar, ai);
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+    VecIO<real, V>::ldg(d.u, idx, ur, ui);
+    if (!a.first) {
+      VecIO<real, V>::ld(d.y, idx, qr, qi);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) qr[v] = qi[v] = 0;
+    }
+    real wr[V], wi[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      wr[v] = fma(sig[v], ar[v], fma(-bsp[v], qr[v], -coef[v] * xr[v]));
+      wi[v] = fma(sig[v], ai[v], fma(-bsp[v], qi[v], -coef[v] * xi[v]));
+    }
+    VecIO<real, V>::st(d.y, idx, wr, wi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
+      pacc[v * kNumPartials + 0] += wr[v] * wr[v] + wi[v] * wi[v];
+      pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];
+      pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
+    }
+  } else if (MODE == kModeUpdate) {
+    real wr[V], wi[V], xr[V], xi[V];
+    VecIO<real, V>::ld(d.y, idx, wr, wi);
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      wr[v] = fma(-coef[v], xr[v], wr[v]);
+      wi[v] = fma(-coef[v], xi[v], wi[v]);
+      pacc[v * kNumPartials] += wr[v] * wr[v] + wi[v] * wi[v];
+    }
+    VecIO<real, V>::st(d.y, idx, wr, wi);
+  } else if (MODE == kModeStartNorm) {
+    real xr[V], xi[V];
+    VecIO<real, V>::ldg(d.x, idx, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) pacc[v * kNumPartials] += xr[v] * xr[v] + xi[v] * xi[v];
+  } else if (MODE == kModeScale) {
+    real xr[V], xi[V];
+    VecIO<real, V>::ld(d.x, idx, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xr[v] *= coef[v];
+      xi[v] *= coef[v];
+    }
+    VecIO<real, V>::st(d.y, idx, xr, xi);
+  }
+}
+
+
 __device__ __forceinline__ int find_instance(const int* tile_start, int n_inst, int tile) {
   if (n_inst == 1) return 0;
   int lo = 0, hi = n_inst - 1;
@@ -90,6 +181,67 @@ __device__ __forceinline__ int find_instance(const int* tile_start, int n_inst, 
   return lo;
 }
 
+
+// pair index of i < j in the triangular pair tables
+__device__ __forceinline__ int tri(int i, int j) { return (j * (j - 1)) / 2 + i; }
+
+// Complex accumulators.  FP32: two packed accumulators updated with the
+// Blackwell f32x2 FMA, a = sum c_re x and b = sum c_im x (x = (re, im)), so a
+// complex multiply-add is two FFMA2 and a real one (the s+ s- coefficients of
+// a symmetric coupling tensor) is one; the value is (a.x - b.y, a.y + b.x).
+// FP64: plain FMAs.
+template <typename real>
+struct Cx;
+
+template <>
+struct Cx<float> {
+  using v2 = float2;
+  float2 a, b;
+  __device__ __forceinline__ void set(float e, float2 x) {
+    a = make_float2(e * x.x, e * x.y);
+    b = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void mac(float cr, float ci, float2 x) {
+    a = __ffma2_rn(make_float2(cr, cr), x, a);
+    b = __ffma2_rn(make_float2(ci, ci), x, b);
+  }
+  __device__ __forceinline__ void mac_re(float cr, float2 x) { a = __ffma2_rn(make_float2(cr, cr), x, a); }
+  __device__ __forceinline__ void add(float2 v) {
+    a.x += v.x;
+    a.y += v.y;
+  }
+  __device__ __forceinline__ float2 value() const { return make_float2(a.x - b.y, a.y + b.x); }
+};
+
+template <>
+struct Cx<double> {
+  using v2 = double2;
+  double re, im;
+  __device__ __forceinline__ void set(double e, double2 x) {
+    re = e * x.x;
+    im = e * x.y;
+  }
+  __device__ __forceinline__ void mac(double cr, double ci, double2 x) {
+    re = fma(cr, x.x, re);
+    re = fma(-ci, x.y, re);
+    im = fma(cr, x.y, im);
+    im = fma(ci, x.x, im);
+  }
+  __device__ __forceinline__ void mac_re(double cr, double2 x) {
+    re = fma(cr, x.x, re);
+    im = fma(cr, x.y, im);
+  }
+  __device__ __forceinline__ void add(double2 v) {
+    re += v.x;
+    im += v.y;
+  }
+  __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
+};
+
+template <typename real>
+__device__ __forceinline__ typename Cx<real>::v2 ldx(const void* x, long long idx) {
+  return __ldg(reinterpret_cast<const typename Cx<real>::v2*>(x) + idx);
+}
 
 // Last CTA: total[inst][r][c] = sum over the CTAs' partials in a fixed order
 // (four interleaved partial sums, combined in a fixed order), one thread per
@@ -118,17 +270,24 @@ __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
     const DevScalars& sc = d.sc;
     const int j = a.step;
     if (a.mode == kModeLanczos || a.mode == kModeEpilogue) {
-      sc.alpha[(size_t)j * R + r] = total_partial(a, inst, r, 0);
-      sc.p[((size_t)j * R + r) * 2] = total_partial(a, inst, r, 1);
-      sc.p[((size_t)j * R + r) * 2 + 1] = total_partial(a, inst, r, 2);
-    } else if (a.mode == kModeUpdate) {
+      sc.alpha[(size_t)j * sc.ss + r] = total_partial(a, inst, r, 0);
+      sc.p[((size_t)j * sc.ss + r) * 2] = total_partial(a, inst, r, 1);
+      sc.p[((size_t)j * sc.ss + r) * 2 + 1] = total_partial(a, inst, r, 2);
+    } else if (a.mode == kModeApply) {  // gather_alpha
+      const double sg = sc.sigma[(size_t)j * sc.ss + r];
+      sc.alpha[(size_t)j * sc.ss + r] = sg * sg * total_partial(a, inst, r, 0);
+    } else if (a.mode == kModeUpdate || a.mode == kModeStep) {
+      if (a.mode == kModeStep) {
+        sc.p[((size_t)j * sc.ss + r) * 2] = total_partial(a, inst, r, 1);
+        sc.p[((size_t)j * sc.ss + r) * 2 + 1] = total_partial(a, inst, r, 2);
+      }
       const double nrm2 = total_partial(a, inst, r, 0);
       const double bnew = sqrt(fmax(nrm2, 0.0));
-      const double al = sc.alpha[(size_t)j * R + r];
-      const double bold = j > 0 ? sc.beta[(size_t)(j - 1) * R + r] : 0.0;
+      const double al = sc.alpha[(size_t)j * sc.ss + r];
+      const double bold = j > 0 ? sc.beta[(size_t)(j - 1) * sc.ss + r] : 0.0;
       double scl = fmax(sc.scale[r], fmax(fabs(al), bold));
       sc.scale[r] = scl;
-      sc.beta[(size_t)j * R + r] = bnew;
+      sc.beta[(size_t)j * sc.ss + r] = bnew;
       double sig = 0.0;
       if (sc.active[r]) {
         if (j < d.M - 1 && (!(bnew > d.tol * scl) || !isfinite(bnew) || !isfinite(al))) {
@@ -138,7 +297,7 @@ __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
           sig = bnew > 0.0 ? 1.0 / bnew : 0.0;
         }
       }
-      sc.sigma[(size_t)(j + 1) * R + r] = sig;
+      sc.sigma[(size_t)(j + 1) * sc.ss + r] = sig;
     } else if (a.mode == kModeStartNorm) {
       const double nrm = sqrt(fmax(total_partial(a, inst, r, 0), 0.0));
       sc.sigma[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;

@@ -65,8 +65,12 @@ void observable_coefs(const HostSystem& hs, const double* u, double out[3]);
 
 // ---- device-side descriptors ------------------------------------------------
 
-// Per-instance Lanczos scalars in device memory; arrays are [M][R] (step major).
+// Per-instance Lanczos scalars in device memory; arrays are [M][ss] (step
+// major) where ss is the scalar row stride: the instance's vectors are
+// columns 0..R-1 of these arrays (the pointers may be offset into a larger
+// [M][R_total] array when every vector of a run is its own instance).
 struct DevScalars {
+  int ss = 0;                // row stride of alpha, beta, p (complex), sigma
   double* alpha = nullptr;   // [M][R]
   double* beta = nullptr;    // [M][R]   norm after step j
   double* p = nullptr;       // [M][R][2]
@@ -103,6 +107,9 @@ enum KernelMode : int {
   kModeApplyS = 4,    // y = scale * (u.S) x  (scale = sigma_0 when Lanczos)
   kModeScale = 5,     // y = sigma_0 x (elementwise; y may equal x)
   kModeEpilogue = 6,  // as kModeLanczos with H q_j read from `hq` instead of gathered (elementwise)
+  kModeStep = 7,      // the whole step after a gather that produced alpha_j (gather_alpha):
+                      // w = sigma_j hq - beta_j sigma_{j-1} q_{j-1} - alpha_j sigma_j q_j (in place in y),
+                      // partials |w|^2, p; then p_j, beta, sigma (elementwise)
 };
 
 struct LaunchArgs {
@@ -136,6 +143,9 @@ struct LaunchArgs {
   int first_pass = 1;   // 1: diagonal, and the output is written; 0: the output is accumulated
   int single_pass = 1;  // 1: the single-pass form (cube on the low K bits, all flags implied)
   int min_blocks = 2;   // register budget of the spin-1/2 kernel: 2 or 3 resident CTAs per SM
+  // kModeApply of the spin-1/2 kernels: also sum Re<x|y> per vector, and the
+  // last CTA sets alpha_j = sigma_j^2 Re<q_j|H q_j> (x = q_j, y = H q_j)
+  int gather_alpha = 0;
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -148,15 +158,19 @@ struct Shape {
   int half_rows = 2;    // spin-1/2 kernel: cubes per thread slot in a row tile
   int half_multipass = 0;  // spin-1/2 kernel: 1 = ceil(N/K) passes whose cubes cover all bits
   int half_min_blocks = 2; // spin-1/2 kernel: register budget of 2 or 3 CTAs per SM
+  int half_vm = 0;         // spin-1/2 kernel: 1 = vector-major Lanczos block (ftlm_run only)
   bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
 };
 
 // Kernel launchers (kernels.cu).  `V` is the number of complex values per
 // thread (2 for c64, 1 for c128).  Return cudaError_t as int.
 int launch_rows(const LaunchArgs& a, int c64, int grid, int threads, size_t smem, void* stream);
+// vector_major: the block is R contiguous vectors of dim values (else dim rows of R values)
 int launch_start_random(const InstDesc* inst_host, const InstDesc* inst_dev, int R, uint64_t seed,
-                        uint64_t vec_offset, void* out, int c64, void* stream);
-int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream);
+                        uint64_t vec_offset, void* out, int c64, void* stream, int vector_major = 0);
+int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream,
+                       int vector_major = 0);
+int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int c64, void* stream);
 int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
 size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads);
 int prepare_rows_kernels(size_t smem);
@@ -169,6 +183,17 @@ int launch_half(const LaunchArgs& a, int K, int c64, int grid, int threads, size
 size_t half_smem_bytes(int n, int K, int rows_per_tile, int threads);
 int prepare_half_kernels(size_t smem);
 int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem, int min_blocks, bool multipass, int R);
+
+// Vector-major spin-1/2 kernel (hv_vm.cu): mode kModeApply over R instances,
+// one per vector (a.tiles_per_vg tiles each), all of one system; K = 3 or 4;
+// a.single_pass = 0: one pass of the multi-pass form (cube_lo, new_lo, first_pass).
+int launch_vm(const LaunchArgs& a, int K, int min_blocks, int c64, int grid, int threads, size_t smem, void* stream);
+size_t vm_smem_bytes(int n, int K, int threads);
+int prepare_vm_kernels(size_t smem);
+int vm_max_ctas_per_sm(int K, int min_blocks, int c64, int threads, size_t smem, bool multipass);
+// kModeStep / kModeStartNorm over the same one-vector instances (256 threads)
+int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream);
+constexpr int kVmLaneBits = 5;  // rows per warp-wide load: 2^5
 
 // Host tridiagonal eigensolver + sums (tridiag.cpp).
 ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,

@@ -36,9 +36,6 @@ namespace ftlm {
 
 namespace {
 
-// pair index of i < j in the triangular table
-__device__ __forceinline__ int tri(int i, int j) { return (j * (j - 1)) / 2 + i; }
-
 template <typename real>
 struct HalfSmem {
   real* cp;     // [npairs][4][2]  coefficient by (bit_i, bit_j) of the row: 0=(0,0) 1=(0,1) 2=(1,0) 3=(1,1)
@@ -82,56 +79,6 @@ size_t half_smem_bytes(int n, int K, int rows_per_tile, int threads) {
   return ((reals * 8 + 15) & ~size_t(15)) + (size_t)threads * 4 * 8;
 }
 
-// Complex accumulators.  FP32: two packed accumulators updated with the
-// Blackwell f32x2 FMA, a = sum c_re x and b = sum c_im x (x = (re, im)), so a
-// complex multiply-add is two FFMA2 and a real one (the s+ s- coefficients of
-// a symmetric coupling tensor) is one; the value is (a.x - b.y, a.y + b.x).
-// FP64: plain FMAs.
-template <typename real>
-struct Cx;
-
-template <>
-struct Cx<float> {
-  using v2 = float2;
-  float2 a, b;
-  __device__ __forceinline__ void set(float e, float2 x) {
-    a = make_float2(e * x.x, e * x.y);
-    b = make_float2(0.f, 0.f);
-  }
-  __device__ __forceinline__ void mac(float cr, float ci, float2 x) {
-    a = __ffma2_rn(make_float2(cr, cr), x, a);
-    b = __ffma2_rn(make_float2(ci, ci), x, b);
-  }
-  __device__ __forceinline__ void mac_re(float cr, float2 x) { a = __ffma2_rn(make_float2(cr, cr), x, a); }
-  __device__ __forceinline__ float2 value() const { return make_float2(a.x - b.y, a.y + b.x); }
-};
-
-template <>
-struct Cx<double> {
-  using v2 = double2;
-  double re, im;
-  __device__ __forceinline__ void set(double e, double2 x) {
-    re = e * x.x;
-    im = e * x.y;
-  }
-  __device__ __forceinline__ void mac(double cr, double ci, double2 x) {
-    re = fma(cr, x.x, re);
-    re = fma(-ci, x.y, re);
-    im = fma(cr, x.y, im);
-    im = fma(ci, x.x, im);
-  }
-  __device__ __forceinline__ void mac_re(double cr, double2 x) {
-    re = fma(cr, x.x, re);
-    im = fma(cr, x.y, im);
-  }
-  __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
-};
-
-template <typename real>
-__device__ __forceinline__ typename Cx<real>::v2 ldx(const void* x, long long idx) {
-  return __ldg(reinterpret_cast<const typename Cx<real>::v2*>(x) + idx);
-}
-
 // RS > 0: the row stride R is the compile-time constant RS; RS = 0: runtime R.
 // MP: one pass of the multi-pass form (cube position and pass flags from the
 // launch arguments); otherwise the single-pass form with the cube on the low
@@ -141,7 +88,9 @@ template <typename real, int K, int MODE, int RS, bool MP, int MINB>
 __global__ void __launch_bounds__(256, MINB) half_kernel(const __grid_constant__ LaunchArgs a) {
   using v2 = typename Cx<real>::v2;
   constexpr int NR = 1 << K;
-  constexpr bool kPartials = MODE == kModeLanczos;
+  // partial sums: alpha and p of the fused step, or Re<x|Hx> of a gather for the split step
+  const bool kPartials = MODE == kModeLanczos || (MODE == kModeApply && !MP && a.gather_alpha);
+  constexpr int NPS = MODE == kModeLanczos ? 3 : 1;  // partial sums in use
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDesc d;
   __shared__ int is_last;
@@ -226,15 +175,15 @@ __global__ void __launch_bounds__(256, MINB) half_kernel(const __grid_constant__
         if ((int)threadIdx.x < Rg && kk < R) {
           double sum[3] = {0, 0, 0};
           for (int sl = 0; sl < slots; ++sl)
-            for (int c = 0; c < 3; ++c) sum[c] += S.red[(threadIdx.x + sl * Rg) * 4 + c];
+            for (int c = 0; c < NPS; ++c) sum[c] += S.red[(threadIdx.x + sl * Rg) * 4 + c];
           double* out = a.partials + ((size_t)blockIdx.x * R + kk) * kNumPartials;
-          for (int c = 0; c < 3; ++c) out[c] = sum[c];
+          for (int c = 0; c < NPS; ++c) out[c] = sum[c];
         }
         for (int c = 0; c < 4; ++c) acc_d[c] = 0.0;
       }
-      if (kPartials && kvalid) {
-        sig = (real)d.sc.sigma[(size_t)a.step * R + k];
-        bsp = a.first ? (real)0 : (real)(d.sc.beta[(size_t)(a.step - 1) * R + k] * d.sc.sigma[(size_t)(a.step - 1) * R + k]);
+      if (MODE == kModeLanczos && kvalid) {
+        sig = (real)d.sc.sigma[(size_t)a.step * d.sc.ss + k];
+        bsp = a.first ? (real)0 : (real)(d.sc.beta[(size_t)(a.step - 1) * d.sc.ss + k] * d.sc.sigma[(size_t)(a.step - 1) * d.sc.ss + k]);
       }
       cur_vg = vg;
     }
@@ -404,6 +353,10 @@ __global__ void __launch_bounds__(256, MINB) half_kernel(const __grid_constant__
             hv.y += prev.y;
           }
           __stcs(yp, hv);
+          if (kPartials) {  // Re <x|Hx>; the own rows are re-read (L1) rather than kept in registers
+            const v2 xv = ldx<real>(x, idx);
+            pacc[0] += xv.x * hv.x + xv.y * hv.y;
+          }
         } else {
           v2 w;
           w.x = sig * hv.x;
@@ -423,7 +376,7 @@ __global__ void __launch_bounds__(256, MINB) half_kernel(const __grid_constant__
       }
     }
     if (kPartials)
-      for (int c = 0; c < 3; ++c) acc_d[c] += (double)pacc[c];
+      for (int c = 0; c < NPS; ++c) acc_d[c] += (double)pacc[c];
   }
   if (!kPartials) return;
   if (cur_vg >= 0) {
@@ -434,9 +387,9 @@ __global__ void __launch_bounds__(256, MINB) half_kernel(const __grid_constant__
     if ((int)threadIdx.x < Rg && kk < R) {
       double sum[3] = {0, 0, 0};
       for (int sl = 0; sl < slots; ++sl)
-        for (int c = 0; c < 3; ++c) sum[c] += S.red[(threadIdx.x + sl * Rg) * 4 + c];
+        for (int c = 0; c < NPS; ++c) sum[c] += S.red[(threadIdx.x + sl * Rg) * 4 + c];
       double* out = a.partials + ((size_t)blockIdx.x * R + kk) * kNumPartials;
-      for (int c = 0; c < 3; ++c) out[c] = sum[c];
+      for (int c = 0; c < NPS; ++c) out[c] = sum[c];
     }
   }
   __threadfence();

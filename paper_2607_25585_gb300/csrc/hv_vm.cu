@@ -1,0 +1,600 @@
+// Vector-major spin-1/2 H.v (Eq. 3 of arxiv 2607.25585 with every s_i = 1/2)
+// for the Lanczos runs.
+//
+// Layout.  Every vector of the run is a contiguous array of d complex values
+// (each vector is its own instance of the launch), so a vector's whole
+// gathered slice -- d * 8 bytes in complex64, 8 MB at d = 2^20 -- stays in L2
+// while its neighbours are read, and a warp's loads are 32 consecutive rows.
+//
+// Thread mapping.  The 32 lanes of a warp hold 32 consecutive rows (bits
+// 0..4 of the row index); each thread owns a register cube along bits
+// [5, 5 + K) for its lane, i.e. 2^K rows of one vector; a warp processes one
+// slab of 2^(5+K) consecutive rows at a time.  Flips of cube bits read
+// registers; every other bit (the lane bits and the slab bits above the cube)
+// is gathered as in the low-bit register-cube kernel: one neighbouring cube
+// per bit j serves the single flip of j and the K mixed pairs (c, j), one per
+// pair of outer bits.  Flips of the lane bits and of the low slab bits land in
+// rows the same CTA has just read (L1).
+//
+// Coefficients.  The single-flip coefficient of site j and the diagonal are
+// sums over bit groups: lane bits (per-system tables indexed by the lane),
+// cube bits (tables indexed by the cube row) and slab bits (computed per slab
+// by the warp's lanes in parallel).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace ftlm {
+
+namespace {
+
+constexpr int kLaneBits = kVmLaneBits;
+
+template <typename real>
+struct VmSmem {
+  real* cp;   // [npairs][4][2] pair coefficients by (bit_i, bit_j) of the row
+  real* fl;   // [n][32][2]  sum_{i < 5} rho_ji m_i(lane)
+  real* fc;   // [n][NR][2]  sum_c rho_{j, 5+c} m_c(r)
+  real* el;   // [32]        diagonal from the lane bits alone
+  real* gl;   // [K][32]     sum_{i < 5} zz_{i, 5+c} m_i(lane)
+  real* ec;   // [NR]        diagonal from the cube bits alone
+  real* ws;   // per warp: fs [n][2], hs [5], gs [K], es [1]
+};
+
+template <typename real>
+__device__ VmSmem<real> vm_carve(unsigned char* raw, int n, int K, int nwarps, int& warp_stride) {
+  VmSmem<real> s;
+  const int NR = 1 << K;
+  real* p = reinterpret_cast<real*>(raw);
+  s.cp = p;
+  p += (n * (n - 1) / 2) * 8;
+  s.fl = p;
+  p += n * 32 * 2;
+  s.fc = p;
+  p += n * NR * 2;
+  s.el = p;
+  p += 32;
+  s.gl = p;
+  p += K * 32;
+  s.ec = p;
+  p += NR;
+  s.ws = p;
+  warp_stride = 2 * n + kLaneBits + K + 1;
+  (void)nwarps;
+  return s;
+}
+
+// zz coefficient of sites (i, j), stored for i < j
+template <typename real>
+__device__ __forceinline__ real zzc(const real* t, const TabLayout& L, int n, int i, int j) {
+  return i < j ? t[L.off_zz + i * n + j] : t[L.off_zz + j * n + i];
+}
+
+}  // namespace
+
+size_t vm_smem_bytes(int n, int K, int threads) {
+  const int NR = 1 << K, nwarps = threads / 32;
+  const size_t reals = (size_t)(n * (n - 1) / 2) * 8 + (size_t)n * 32 * 2 + (size_t)n * NR * 2 + 32 + (size_t)K * 32 + NR +
+                       (size_t)nwarps * (2 * n + kLaneBits + K + 1);
+  return reals * 8;  // sized for double tables
+}
+
+// MP: one pass of the multi-pass form.  The cube spans bits [a.cube_lo,
+// a.cube_lo + K) (>= 5); cube bits >= a.new_lo are the pass's own: their single
+// flips, their pairs with each other and their mixed pairs with the lane bits
+// and with the bits above the cube.  The first pass (cube on bits [5, 5 + K))
+// also does the diagonal, the lane bits' single flips and the lane-lane pairs
+// and writes the output; later passes add to it.  With ceil((n - 5) / K) passes
+// whose cubes cover bits [5, n), every pair is a cube pair, a mixed pair or a
+// lane-lane pair of exactly one pass, so each gathered load serves K (or K + 1)
+// multiply-adds per row instead of one.
+// Without MP: one pass, cube on bits [5, 5 + K), every term; pairs of two bits
+// outside the cube cost one gathered load per multiply-add.
+// MINB: resident CTAs per SM the register allocator must allow.
+template <typename real, int K, bool MP, int MINB>
+__global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ LaunchArgs a) {
+  using v2 = typename Cx<real>::v2;
+  constexpr int NR = 1 << K;
+  constexpr int CB = kLaneBits;  // lane bits [0, CB)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ InstDesc d;
+  __shared__ double red[32];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool kPartials = a.gather_alpha != 0;  // Re<x|Hx> per vector, then alpha_j
+  const InstDesc* insts = a.inline_one ? &a.one : a.inst;
+  if (threadIdx.x == 0) d = insts[0];
+  __syncthreads();
+  const int n = d.n;
+  const int s0 = MP ? a.cube_lo : CB;          // cube bits [s0, s0 + K)
+  const int cnew = MP ? a.new_lo - s0 : 0;     // first own cube bit (cube-relative)
+  const bool first = MP ? a.first_pass != 0 : true;
+  int wstride = 0;
+  const VmSmem<real> S = vm_carve<real>(smem_raw, n, K, nwarps, wstride);
+  const real* t = reinterpret_cast<const real*>(d.tab);  // every instance of the launch shares the system
+  const TabLayout& L = d.lay;
+  const int bd = blockDim.x;
+  auto in_cube = [&](int i) { return i >= s0 && i < s0 + K; };
+  // cube bits below new_lo (the overlap of the last pass with the one before)
+  // belong to an earlier pass: their terms get zero coefficients here
+  auto done = [&](int i) { return MP && i >= s0 && i < s0 + cnew; };
+
+  // ---- per-system tables ----
+  for (int q = threadIdx.x; q < n * n; q += bd) {
+    const int i = q / n, j = q % n;
+    if (i >= j) continue;
+    const int ij = i * n + j;
+    const real pmr = t[L.off_pm + 2 * ij], pmi = t[L.off_pm + 2 * ij + 1];
+    const real ppr = t[L.off_pp + 2 * ij], ppi = t[L.off_pp + 2 * ij + 1];
+    real* c = S.cp + tri(i, j) * 8;
+    const real z = (done(i) || done(j)) ? (real)0 : (real)1;
+    c[0] = z * ppr; c[1] = -z * ppi;   // (0,0): mu = s-_i s-_j nu
+    c[2] = z * pmr; c[3] = -z * pmi;   // (0,1): mu = s-_i s+_j nu
+    c[4] = z * pmr; c[5] = z * pmi;    // (1,0): mu = s+_i s-_j nu
+    c[6] = z * ppr; c[7] = z * ppi;    // (1,1): mu = s+_i s+_j nu
+  }
+  for (int q = threadIdx.x; q < n * 32; q += bd) {  // lane part of F_j
+    const int j = q / 32, l = q % 32;
+    real fr = 0, fi = 0;
+    for (int i = 0; i < CB && !done(j); ++i) {
+      const real mi = ((l >> i) & 1) ? (real)0.5 : (real)-0.5;
+      fr += t[L.off_rho + 2 * (j * n + i)] * mi;
+      fi += t[L.off_rho + 2 * (j * n + i) + 1] * mi;
+    }
+    S.fl[2 * q] = fr;
+    S.fl[2 * q + 1] = fi;
+  }
+  for (int q = threadIdx.x; q < n * NR; q += bd) {  // cube part of F_j
+    const int j = q / NR, r = q % NR;
+    real fr = 0, fi = 0;
+    for (int c = 0; c < K && !done(j); ++c) {
+      const real mc = ((r >> c) & 1) ? (real)0.5 : (real)-0.5;
+      fr += t[L.off_rho + 2 * (j * n + s0 + c)] * mc;
+      fi += t[L.off_rho + 2 * (j * n + s0 + c) + 1] * mc;
+    }
+    S.fc[2 * q] = fr;
+    S.fc[2 * q + 1] = fi;
+  }
+  if (first) {
+    for (int l = threadIdx.x; l < 32; l += bd) {  // lane bits: diagonal and cross terms with the cube
+      real e = 0;
+      for (int i = 0; i < CB; ++i) {
+        const int bi = (l >> i) & 1;
+        const real mi = bi ? (real)0.5 : (real)-0.5;
+        e += t[L.off_hz + i] * mi + t[L.off_iondiag + i * L.qmax + bi];
+        for (int i2 = i + 1; i2 < CB; ++i2) e += zzc(t, L, n, i, i2) * mi * (((l >> i2) & 1) ? (real)0.5 : (real)-0.5);
+      }
+      S.el[l] = e;
+      for (int c = 0; c < K; ++c) {
+        real g = 0;
+        for (int i = 0; i < CB; ++i) g += zzc(t, L, n, i, s0 + c) * (((l >> i) & 1) ? (real)0.5 : (real)-0.5);
+        S.gl[c * 32 + l] = g;
+      }
+    }
+    for (int r = threadIdx.x; r < NR; r += bd) {  // cube bits alone
+      real e = 0;
+      for (int c = 0; c < K; ++c) {
+        const int bc = (r >> c) & 1;
+        const real mc = bc ? (real)0.5 : (real)-0.5;
+        e += t[L.off_hz + s0 + c] * mc + t[L.off_iondiag + (s0 + c) * L.qmax + bc];
+        for (int c2 = c + 1; c2 < K; ++c2)
+          e += zzc(t, L, n, s0 + c, s0 + c2) * mc * (((r >> c2) & 1) ? (real)0.5 : (real)-0.5);
+      }
+      S.ec[r] = e;
+    }
+  }
+  __syncthreads();
+
+  real* W = S.ws + warp * wstride;  // this warp's unit tables
+  real* fs = W;                     // [n][2]
+  real* hs = W + 2 * n;             // [5]
+  real* gs = hs + CB;               // [K]
+  real* es = gs + K;                // [1]
+  // a unit: 32 lanes x the cube = 2^(5+K) rows whose other ("outer") bits are fixed
+  const long long nunits = d.dim >> (CB + K);
+  const int units_per_tile = a.rows_per_tile >> (CB + K);
+  const unsigned long long lowmask = (1ull << (s0 - CB)) - 1ull;  // outer bits between the lanes and the cube
+  const int nnb = CB + n - s0 - K;  // neighbour bits: the lane bits and the bits above the cube
+  const bool real_fast_pm = a.real_pm != 0;
+  if (kPartials)  // this CTA's slot of every vector: [vector][CTA][kNumPartials]
+    for (int k = threadIdx.x; k < a.n_inst * kNumPartials; k += bd)
+      a.partials[((size_t)(k / kNumPartials) * gridDim.x + blockIdx.x) * kNumPartials + k % kNumPartials] = 0.0;
+  // the CTA's sum of its threads' Re<x|Hx> for vector `inst`, in a fixed order
+  auto flush = [&](int inst, double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nwarps; ++w) tot += red[w];
+      a.partials[((size_t)inst * gridDim.x + blockIdx.x) * kNumPartials] = tot;
+    }
+    __syncthreads();
+  };
+  double adot = 0.0;
+  int cur = -1;
+  const void* x = nullptr;
+  void* y = nullptr;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int inst = tile / a.tiles_per_vg;  // tiles are vector-major: every vector has tiles_per_vg of them
+    if (inst != cur) {  // per-vector pointers (the tables are shared)
+      if (kPartials && cur >= 0) flush(cur, adot);
+      adot = 0.0;
+      x = insts[inst].x;
+      y = insts[inst].y;
+      cur = inst;
+    }
+    const long long unit0 = (long long)(tile - inst * a.tiles_per_vg) * units_per_tile;
+    for (int ui = warp; ui < units_per_tile; ui += nwarps) {
+      const unsigned long long u = (unsigned long long)(unit0 + ui);
+      if ((long long)u >= nunits) break;
+      const unsigned long long base = ((u >> (s0 - CB)) << (s0 + K)) | ((u & lowmask) << CB);
+      // unit tables (the outer bits' share of the coefficients), the warp's lanes in parallel
+      __syncwarp();
+      for (int j = lane; j < n; j += 32) {
+        const real z = done(j) ? (real)0 : (real)1;
+        real fr = z * t[L.off_hp + 2 * j], fi = z * t[L.off_hp + 2 * j + 1];
+        for (int i = CB; i < n && !done(j); ++i) {
+          if (in_cube(i)) continue;
+          const real mi = ((base >> i) & 1ull) ? (real)0.5 : (real)-0.5;
+          fr += t[L.off_rho + 2 * (j * n + i)] * mi;
+          fi += t[L.off_rho + 2 * (j * n + i) + 1] * mi;
+        }
+        fs[2 * j] = fr;
+        fs[2 * j + 1] = fi;
+      }
+      if (first) {
+        if (lane < CB) {  // lane bit `lane` x outer bits
+          real h = 0;
+          for (int j = CB; j < n; ++j)
+            if (!in_cube(j)) h += zzc(t, L, n, lane, j) * (((base >> j) & 1ull) ? (real)0.5 : (real)-0.5);
+          hs[lane] = h;
+        } else if (lane < CB + K) {  // cube bit x outer bits
+          const int c = lane - CB;
+          real g = 0;
+          for (int i = CB; i < n; ++i)
+            if (!in_cube(i)) g += zzc(t, L, n, s0 + c, i) * (((base >> i) & 1ull) ? (real)0.5 : (real)-0.5);
+          gs[c] = g;
+        }
+        // diagonal of the outer bits alone: lane i adds the terms of outer bit i
+        // (Zeeman, single-ion, zz with the outer bits above i), then a warp sum
+        real e = 0;
+        for (int i = lane; i < n; i += 32) {
+          if (i < CB || in_cube(i)) continue;
+          const int bi = (base >> i) & 1ull;
+          real zs = t[L.off_hz + i];
+          for (int j = i + 1; j < n; ++j)
+            if (!in_cube(j)) zs += zzc(t, L, n, i, j) * (((base >> j) & 1ull) ? (real)0.5 : (real)-0.5);
+          e += (bi ? (real)0.5 : (real)-0.5) * zs + t[L.off_iondiag + i * L.qmax + bi];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0) es[0] = e;
+      }
+      __syncwarp();
+      const long long row0 = (long long)(base | (unsigned long long)lane);
+      if (!first)  // the earlier passes' sums are read at the end of the unit: bring them to L2 now
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const v2*>(y) + row0 + ((long long)r << s0)));
+      v2 xo[NR];
+      Cx<real> acc[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) xo[r] = ldx<real>(x, row0 + ((long long)r << s0));
+      if (first) {  // diagonal
+        real eo = S.el[lane] + es[0];
+#pragma unroll
+        for (int i = 0; i < CB; ++i) eo += (((lane >> i) & 1) ? (real)0.5 : (real)-0.5) * hs[i];
+        real g[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) g[c] = S.gl[c * 32 + lane] + gs[c];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          real e = eo + S.ec[r];
+#pragma unroll
+          for (int c = 0; c < K; ++c) e += ((r >> c) & 1) ? (real)0.5 * g[c] : (real)-0.5 * g[c];
+          acc[r].set(e, xo[r]);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r].set((real)0, xo[r]);
+      }
+      // own cube bits: single flips and pairs in registers
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const int sc = s0 + c;
+        const real br = fs[2 * sc] + S.fl[2 * (sc * 32 + lane)], bi = fs[2 * sc + 1] + S.fl[2 * (sc * 32 + lane) + 1];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const real fr = br + S.fc[2 * (sc * NR + r)];
+          const real fim = bi + S.fc[2 * (sc * NR + r) + 1];
+          acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
+        }
+#pragma unroll
+        for (int c1 = 0; c1 < c; ++c1) {
+          const real* cp = S.cp + tri(s0 + c1, sc) * 8;
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const int idx = 2 * ((r >> c1) & 1) + ((r >> c) & 1);
+            acc[r].mac(cp[2 * idx], cp[2 * idx + 1], xo[r ^ (1 << c) ^ (1 << c1)]);
+          }
+        }
+      }
+      // neighbour bit j (a lane bit, or a bit above the cube): the neighbouring
+      // cube serves the mixed pairs (c, j) and, where this pass owns it, the
+      // single flip of j
+      for (int jj = 0; jj < nnb; ++jj) {
+        const int j = jj < CB ? jj : s0 + K + (jj - CB);
+        const int bj = (int)((row0 >> j) & 1);
+        const long long nb = row0 ^ (1ll << j);
+        v2 yv[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) yv[r] = ldx<real>(x, nb + ((long long)r << s0));
+        if (MP && jj + 1 < nnb) {  // the next neighbour cube to L1 while this one is used
+          const int jn = jj + 1 < CB ? jj + 1 : s0 + K + (jj + 1 - CB);
+          if (jn >= CB) {  // (the lane-bit neighbours share the own rows' lines)
+            const v2* nx = reinterpret_cast<const v2*>(x) + (row0 ^ (1ll << jn));
+#pragma unroll
+            for (int r = 0; r < NR; ++r) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + ((long long)r << s0)));
+          }
+        }
+        if (!MP || (first && j < CB)) {
+          const real br = fs[2 * j] + S.fl[2 * (j * 32 + lane)], bi = fs[2 * j + 1] + S.fl[2 * (j * 32 + lane) + 1];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const real fim = bi + S.fc[2 * (j * NR + r) + 1];
+            acc[r].mac(br + S.fc[2 * (j * NR + r)], bj ? fim : -fim, yv[r]);
+          }
+        }
+        const bool uniform = j >= CB;  // bit j (above the cube) is the same for the whole warp
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          const int sc = s0 + c;
+          // pair (min, max) and the row's bits in that order
+          const real* cp = S.cp + (j < sc ? tri(j, sc) : tri(sc, j)) * 8;
+          if (uniform && real_fast_pm) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              const int bc = (r >> c) & 1;
+              const int idx = 2 * bc + bj;  // j > sc here
+              if (bc != bj) acc[r].mac_re(cp[2 * idx], yv[r ^ (1 << c)]);
+              else acc[r].mac(cp[2 * idx], cp[2 * idx + 1], yv[r ^ (1 << c)]);
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              const int bc = (r >> c) & 1;
+              const int idx = j < sc ? 2 * bj + bc : 2 * bc + bj;
+              acc[r].mac(cp[2 * idx], cp[2 * idx + 1], yv[r ^ (1 << c)]);
+            }
+          }
+        }
+      }
+      // pairs of two neighbour bits: one coefficient for the whole cube (without
+      // MP every such pair; with MP only the lane-lane pairs, in the first pass)
+      if (first) {
+        const int npb = MP ? CB : nnb;
+        for (int jj = 1; jj < npb; ++jj) {
+          const int j = jj < CB ? jj : s0 + K + (jj - CB);
+          const int bj = (int)((row0 >> j) & 1);
+#pragma unroll 2
+          for (int ii = 0; ii < jj; ++ii) {
+            const int i = ii < CB ? ii : s0 + K + (ii - CB);
+            const int bi = (int)((row0 >> i) & 1);
+            const real* cp = S.cp + tri(i, j) * 8 + 2 * (2 * bi + bj);
+            const real cr = cp[0], ci = cp[1];
+            const long long nb = row0 ^ (1ll << i) ^ (1ll << j);
+            v2 yv[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) yv[r] = ldx<real>(x, nb + ((long long)r << s0));
+            if (i >= CB && real_fast_pm && bi != bj) {  // warp-uniform and real
+#pragma unroll
+              for (int r = 0; r < NR; ++r) acc[r].mac_re(cr, yv[r]);
+            } else {
+#pragma unroll
+              for (int r = 0; r < NR; ++r) acc[r].mac(cr, ci, yv[r]);
+            }
+          }
+        }
+      }
+      real pd = 0;
+      v2* const yb = reinterpret_cast<v2*>(y) + row0;
+      if (!first) {  // add the earlier passes' sums: all loads first, then the stores
+        v2 prev[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) prev[r] = __ldcs(yb + ((long long)r << s0));
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r].add(prev[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        v2* yp = yb + ((long long)r << s0);
+        const v2 hv = acc[r].value();
+        __stcs(yp, hv);
+        if (kPartials) {  // the own rows are re-read (L1) rather than kept in registers
+          const v2 xv = ldx<real>(x, row0 + ((long long)r << s0));
+          pd += xv.x * hv.x + xv.y * hv.y;
+        }
+      }
+      adot += (double)pd;
+    }
+  }
+  if (!kPartials) return;
+  if (cur >= 0) flush(cur, adot);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  finalize(a, insts);
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// Streaming modes (kModeStep, kModeStartNorm) on the vector-major block: R
+// one-vector instances, tiles of a.rows_per_tile consecutive elements of one
+// vector (a.tiles_per_vg per vector); a thread moves 16 bytes per array and
+// item (two complex64 or one complex128 value).
+template <typename real, int MODE>
+__global__ void __launch_bounds__(256) vm_stream_kernel(const __grid_constant__ LaunchArgs a) {
+  constexpr int V = sizeof(real) == 4 ? 2 : 1;
+  __shared__ InstDesc d;
+  __shared__ double red[32][kNumPartials];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int bd = blockDim.x;
+  for (int k = threadIdx.x; k < a.n_inst * kNumPartials; k += bd)
+    a.partials[((size_t)(k / kNumPartials) * gridDim.x + blockIdx.x) * kNumPartials + k % kNumPartials] = 0.0;
+  double acc[3] = {0.0, 0.0, 0.0};
+  auto flush = [&](int inst) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][c] = v;
+      acc[c] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps; ++w) t += red[w][threadIdx.x];
+      a.partials[((size_t)inst * gridDim.x + blockIdx.x) * kNumPartials + threadIdx.x] = t;
+    }
+    __syncthreads();
+  };
+  int cur = -1;
+  real sig[V], bsp[V], coef[V];
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int inst = tile / a.tiles_per_vg;
+    if (inst != cur) {
+      if (cur >= 0) flush(cur);
+      if (threadIdx.x == 0) d = a.inst[inst];
+      __syncthreads();
+      const int j = a.step;
+      real sg = 0, bs = 0, cf = 0;
+      if (MODE == kModeStep) {
+        sg = (real)d.sc.sigma[(size_t)j * d.sc.ss];
+        if (!a.first) bs = (real)(d.sc.beta[(size_t)(j - 1) * d.sc.ss] * d.sc.sigma[(size_t)(j - 1) * d.sc.ss]);
+        cf = (real)(d.sc.alpha[(size_t)j * d.sc.ss] * d.sc.sigma[(size_t)j * d.sc.ss]);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        sig[v] = sg;
+        bsp[v] = bs;
+        coef[v] = cf;
+      }
+      cur = inst;
+    }
+    const long long e0 = (long long)(tile - inst * a.tiles_per_vg) * a.rows_per_tile;
+    const long long e_end = min(e0 + (long long)a.rows_per_tile, d.dim);
+    real pacc[V * kNumPartials];
+#pragma unroll
+    for (int k = 0; k < V * kNumPartials; ++k) pacc[k] = 0;
+    const long long step = (long long)bd * V;
+    long long e = e0 + (long long)threadIdx.x * V;
+    for (; e + step < e_end; e += 2 * step) {
+      elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
+      elementwise_item<real, V, MODE>(d, a, e + step, sig, bsp, coef, pacc);
+    }
+    if (e < e_end) elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      real t = 0;
+#pragma unroll
+      for (int v = 0; v < V; ++v) t += pacc[v * kNumPartials + c];
+      acc[c] += (double)t;
+    }
+  }
+  if (cur >= 0) flush(cur);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  finalize(a, a.inst);
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (a.inline_one || (a.rows_per_tile & 1)) return (int)cudaErrorInvalidValue;
+  if (a.mode == kModeStep) {
+    if (c64) vm_stream_kernel<float, kModeStep><<<grid, 256, 0, st>>>(a);
+    else vm_stream_kernel<double, kModeStep><<<grid, 256, 0, st>>>(a);
+  } else if (a.mode == kModeStartNorm) {
+    if (c64) vm_stream_kernel<float, kModeStartNorm><<<grid, 256, 0, st>>>(a);
+    else vm_stream_kernel<double, kModeStartNorm><<<grid, 256, 0, st>>>(a);
+  } else {
+    return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+template <typename real, int K>
+static int launch_vm_k(const LaunchArgs& a, int minb, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (!a.single_pass) vm_kernel<real, K, true, 2><<<grid, threads, smem, st>>>(a);
+  else if (minb > 2) vm_kernel<real, K, false, 3><<<grid, threads, smem, st>>>(a);
+  else vm_kernel<real, K, false, 2><<<grid, threads, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_vm(const LaunchArgs& a, int K, int minb, int c64, int grid, int threads, size_t smem, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (a.mode != kModeApply) return (int)cudaErrorInvalidValue;
+  if (c64) {
+    if (K == 3) return launch_vm_k<float, 3>(a, minb, grid, threads, smem, st);
+    if (K == 4) return launch_vm_k<float, 4>(a, minb, grid, threads, smem, st);
+  } else {
+    if (K == 3) return launch_vm_k<double, 3>(a, minb, grid, threads, smem, st);
+    if (K == 4) return launch_vm_k<double, 4>(a, minb, grid, threads, smem, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <typename real, int K>
+static void vm_variants(std::vector<const void*>& ks) {
+  ks.push_back((const void*)vm_kernel<real, K, false, 2>);
+  ks.push_back((const void*)vm_kernel<real, K, false, 3>);
+  ks.push_back((const void*)vm_kernel<real, K, true, 2>);
+}
+
+int prepare_vm_kernels(size_t smem) {
+  std::vector<const void*> ks;
+  vm_variants<float, 3>(ks);
+  vm_variants<float, 4>(ks);
+  vm_variants<double, 3>(ks);
+  vm_variants<double, 4>(ks);
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
+}
+
+template <typename real, int K>
+static cudaError_t vm_occ(int* nb, int minb, bool multipass, int threads, size_t smem) {
+  if (multipass) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, vm_kernel<real, K, true, 2>, threads, smem);
+  if (minb > 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, vm_kernel<real, K, false, 3>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, vm_kernel<real, K, false, 2>, threads, smem);
+}
+
+int vm_max_ctas_per_sm(int K, int minb, int c64, int threads, size_t smem, bool multipass) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (c64) {
+    if (K == 3) e = vm_occ<float, 3>(&nb, minb, multipass, threads, smem);
+    if (K == 4) e = vm_occ<float, 4>(&nb, minb, multipass, threads, smem);
+  } else {
+    if (K == 3) e = vm_occ<double, 3>(&nb, minb, multipass, threads, smem);
+    if (K == 4) e = vm_occ<double, 4>(&nb, minb, multipass, threads, smem);
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+}  // namespace ftlm

@@ -243,74 +243,14 @@ __device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst,
 // ---------------------------------------------------------------------------
 // the tile loop shared by every mode
 // ---------------------------------------------------------------------------
-// One element group (V values of one row) of the elementwise modes.
-template <typename real, int V, int MODE>
-__device__ __forceinline__ void elementwise_item(const InstDesc& d, const LaunchArgs& a, long long idx,
-                                                 const real* sig, const real* bsp, const real* coef, real* pacc) {
-  if (MODE == kModeEpilogue) {  // w = sigma H q_j - beta sigma' q_{j-1}; alpha and p partials
-    real ar[V], ai[V], xr[V], xi[V], wr[V], wi[V], ur[V], ui[V];
-    VecIO<real, V>::ldg(d.hq, idx, ar, ai);
-    VecIO<real, V>::ldg(d.x, idx, xr, xi);
-    VecIO<real, V>::ldg(d.u, idx, ur, ui);
-    if (!a.first) {
-      real qr[V], qi[V];
-      VecIO<real, V>::ld(d.y, idx, qr, qi);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        wr[v] = fma(sig[v], ar[v], -bsp[v] * qr[v]);
-        wi[v] = fma(sig[v], ai[v], -bsp[v] * qi[v]);
-      }
-    } else {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        wr[v] = sig[v] * ar[v];
-        wi[v] = sig[v] * ai[v];
-      }
-    }
-    VecIO<real, V>::st(d.y, idx, wr, wi);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
-      pacc[v * kNumPartials + 0] += vr * wr[v] + vi * wi[v];
-      pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];
-      pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
-    }
-  } else if (MODE == kModeUpdate) {
-    real wr[V], wi[V], xr[V], xi[V];
-    VecIO<real, V>::ld(d.y, idx, wr, wi);
-    VecIO<real, V>::ldg(d.x, idx, xr, xi);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      wr[v] = fma(-coef[v], xr[v], wr[v]);
-      wi[v] = fma(-coef[v], xi[v], wi[v]);
-      pacc[v * kNumPartials] += wr[v] * wr[v] + wi[v] * wi[v];
-    }
-    VecIO<real, V>::st(d.y, idx, wr, wi);
-  } else if (MODE == kModeStartNorm) {
-    real xr[V], xi[V];
-    VecIO<real, V>::ldg(d.x, idx, xr, xi);
-#pragma unroll
-    for (int v = 0; v < V; ++v) pacc[v * kNumPartials] += xr[v] * xr[v] + xi[v] * xi[v];
-  } else if (MODE == kModeScale) {
-    real xr[V], xi[V];
-    VecIO<real, V>::ld(d.x, idx, xr, xi);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      xr[v] *= coef[v];
-      xi[v] *= coef[v];
-    }
-    VecIO<real, V>::st(d.y, idx, xr, xi);
-  }
-}
-
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SmemView s = carve<real>(smem_raw, a, V);
   __shared__ InstDesc d;
   __shared__ int is_last;
-  constexpr bool kPartials =
-      MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate || MODE == kModeStartNorm;
+  constexpr bool kPartials = MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate ||
+                             MODE == kModeStartNorm || MODE == kModeStep;
   const InstDesc* insts = a.inline_one ? &a.one : a.inst;
   constexpr int NP = V * kNumPartials;
   double acc[NP];
@@ -342,11 +282,13 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
       for (int v = 0; v < V; ++v) {
         const int k = min(col + v, a.R - 1);
         sig[v] = bsp[v] = coef[v] = 0;
-        if (MODE == kModeLanczos || MODE == kModeEpilogue) {
-          sig[v] = (real)d.sc.sigma[(size_t)j * a.R + k];
-          if (!a.first) bsp[v] = (real)(d.sc.beta[(size_t)(j - 1) * a.R + k] * d.sc.sigma[(size_t)(j - 1) * a.R + k]);
+        if (MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeStep) {
+          sig[v] = (real)d.sc.sigma[(size_t)j * d.sc.ss + k];
+          if (!a.first) bsp[v] = (real)(d.sc.beta[(size_t)(j - 1) * d.sc.ss + k] * d.sc.sigma[(size_t)(j - 1) * d.sc.ss + k]);
+          if (MODE == kModeStep)
+            coef[v] = (real)(d.sc.alpha[(size_t)j * d.sc.ss + k] * d.sc.sigma[(size_t)j * d.sc.ss + k]);
         } else if (MODE == kModeUpdate) {
-          coef[v] = (real)(d.sc.alpha[(size_t)j * a.R + k] * d.sc.sigma[(size_t)j * a.R + k]);
+          coef[v] = (real)(d.sc.alpha[(size_t)j * d.sc.ss + k] * d.sc.sigma[(size_t)j * d.sc.ss + k]);
         } else if (MODE == kModeApplyS) {
           coef[v] = a.use_sigma0 ? (real)d.sc.sigma[k] : (real)1;
         } else if (MODE == kModeScale) {
@@ -362,8 +304,8 @@ __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ Launc
     real pacc[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) pacc[k] = 0;
-    constexpr bool kElementwise =
-        MODE == kModeEpilogue || MODE == kModeUpdate || MODE == kModeStartNorm || MODE == kModeScale;
+    constexpr bool kElementwise = MODE == kModeEpilogue || MODE == kModeUpdate || MODE == kModeStartNorm ||
+                                  MODE == kModeScale || MODE == kModeStep;
     if (kElementwise) {
       // element e = row * R + col: linear over the tile; blockDim * V is a
       // multiple of R, so each thread keeps its vector chunk
@@ -503,14 +445,15 @@ __device__ __forceinline__ double unit53(unsigned hi, unsigned lo) {
   return ((double)k + 1.0) * (1.0 / 9007199254740992.0);
 }
 
-template <typename real>
+// VMAJ: vector-major output (element e = k * dim + nu), else row-major (e = nu * R + k).
+template <typename real, bool VMAJ>
 __global__ void start_random_kernel(long long dim, int R, unsigned long long seed, unsigned long long vec_offset,
                                     real* out) {
   const long long total = dim * R;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long nu = e / R;
-    const unsigned long long rg = vec_offset + (unsigned long long)(e - nu * R);
+    const long long nu = VMAJ ? e % dim : e / R;
+    const unsigned long long rg = vec_offset + (unsigned long long)(VMAJ ? e / dim : e - nu * R);
     unsigned c[4] = {(unsigned)nu, (unsigned)((unsigned long long)nu >> 32), (unsigned)rg, (unsigned)(rg >> 32)};
     philox4x32_10(c, (unsigned)seed, (unsigned)(seed >> 32));
     const double u1 = unit53(c[0], c[1]);
@@ -523,13 +466,13 @@ __global__ void start_random_kernel(long long dim, int R, unsigned long long see
   }
 }
 
-template <typename real>
+template <typename real, bool VMAJ>
 __global__ void start_basis_kernel(long long dim, int R, unsigned long long basis_offset, real* out) {
   const long long total = dim * R;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long nu = e / R;
-    const long long k = e - nu * R;
+    const long long nu = VMAJ ? e % dim : e / R;
+    const long long k = VMAJ ? e / dim : e - nu * R;
     out[2 * e] = (real)((unsigned long long)nu == basis_offset + (unsigned long long)k ? 1.0 : 0.0);
     out[2 * e + 1] = (real)0;
   }
@@ -560,7 +503,7 @@ static int allow_smem(int bytes) {
   const void* ks[] = {(const void*)rows_kernel<real, V, kModeApply>, (const void*)rows_kernel<real, V, kModeLanczos>,
                       (const void*)rows_kernel<real, V, kModeUpdate>, (const void*)rows_kernel<real, V, kModeStartNorm>,
                       (const void*)rows_kernel<real, V, kModeApplyS>, (const void*)rows_kernel<real, V, kModeScale>,
-                      (const void*)rows_kernel<real, V, kModeEpilogue>};
+                      (const void*)rows_kernel<real, V, kModeEpilogue>, (const void*)rows_kernel<real, V, kModeStep>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
@@ -587,6 +530,7 @@ static int launch_mode(const LaunchArgs& a, int grid, int threads, size_t smem, 
     case kModeApplyS: return launch_one<real, V, kModeApplyS>(a, grid, threads, smem, st);
     case kModeScale: return launch_one<real, V, kModeScale>(a, grid, threads, smem, st);
     case kModeEpilogue: return launch_one<real, V, kModeEpilogue>(a, grid, threads, smem, st);
+    case kModeStep: return launch_one<real, V, kModeStep>(a, grid, threads, smem, st);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -609,26 +553,73 @@ int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int mode) {
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
+static int elementwise_grid(long long total) {
+  const long long want = (total + 255) / 256;
+  return (int)(want < 152LL * 16 ? want : 152LL * 16);
+}
+
 int launch_start_random(const InstDesc* inst_host, const InstDesc*, int R, uint64_t seed, uint64_t vec_offset,
-                        void* out, int c64, void* stream) {
+                        void* out, int c64, void* stream, int vector_major) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const long long total = inst_host->dim * R;
-  const int threads = 256;
-  const long long want = (total + threads - 1) / threads;
-  const int grid = (int)(want < 152LL * 16 ? want : 152LL * 16);
-  if (c64) start_random_kernel<float><<<grid, threads, 0, st>>>(inst_host->dim, R, seed, vec_offset, (float*)out);
-  else start_random_kernel<double><<<grid, threads, 0, st>>>(inst_host->dim, R, seed, vec_offset, (double*)out);
+  const long long dim = inst_host->dim;
+  const int grid = elementwise_grid(dim * R);
+  if (c64) {
+    if (vector_major) start_random_kernel<float, true><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, (float*)out);
+    else start_random_kernel<float, false><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, (float*)out);
+  } else {
+    if (vector_major) start_random_kernel<double, true><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, (double*)out);
+    else start_random_kernel<double, false><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, (double*)out);
+  }
   return (int)cudaGetLastError();
 }
 
-int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream) {
+int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream,
+                       int vector_major) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const long long total = dim * R;
-  const int threads = 256;
-  const long long want = (total + threads - 1) / threads;
-  const int grid = (int)(want < 152LL * 16 ? want : 152LL * 16);
-  if (c64) start_basis_kernel<float><<<grid, threads, 0, st>>>(dim, R, basis_offset, (float*)out);
-  else start_basis_kernel<double><<<grid, threads, 0, st>>>(dim, R, basis_offset, (double*)out);
+  const int grid = elementwise_grid(dim * R);
+  if (c64) {
+    if (vector_major) start_basis_kernel<float, true><<<grid, 256, 0, st>>>(dim, R, basis_offset, (float*)out);
+    else start_basis_kernel<float, false><<<grid, 256, 0, st>>>(dim, R, basis_offset, (float*)out);
+  } else {
+    if (vector_major) start_basis_kernel<double, true><<<grid, 256, 0, st>>>(dim, R, basis_offset, (double*)out);
+    else start_basis_kernel<double, false><<<grid, 256, 0, st>>>(dim, R, basis_offset, (double*)out);
+  }
+  return (int)cudaGetLastError();
+}
+
+// dst[k * dim + nu] = src[nu * R + k]: a row-major block to the vector-major
+// layout.  Each CTA moves a 32-row x 32-vector tile through shared memory so
+// that both the reads and the writes are coalesced.
+template <typename v2>
+__global__ void to_vector_major_kernel(const v2* __restrict__ src, v2* __restrict__ dst, long long dim, int R) {
+  __shared__ v2 tile[32][33];
+  const long long row_tiles = (dim + 31) / 32;
+  const int vec_tiles = (R + 31) / 32;
+  for (long long t = blockIdx.x; t < row_tiles * vec_tiles; t += gridDim.x) {
+    const long long nu0 = (t / vec_tiles) * 32;
+    const int k0 = (int)(t % vec_tiles) * 32;
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const long long nu = nu0 + i;
+      const int k = k0 + threadIdx.x;
+      if (nu < dim && k < R) tile[i][threadIdx.x] = src[nu * R + k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int k = k0 + i;
+      const long long nu = nu0 + threadIdx.x;
+      if (nu < dim && k < R) dst[(long long)k * dim + nu] = tile[threadIdx.x][i];
+    }
+  }
+}
+
+int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int c64, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long tiles = ((dim + 31) / 32) * ((R + 31) / 32);
+  const int grid = (int)(tiles < 152LL * 16 ? tiles : 152LL * 16);
+  const dim3 block(32, 8);
+  if (c64) to_vector_major_kernel<float2><<<grid, block, 0, st>>>((const float2*)src, (float2*)dst, dim, R);
+  else to_vector_major_kernel<double2><<<grid, block, 0, st>>>((const double2*)src, (double2*)dst, dim, R);
   return (int)cudaGetLastError();
 }
 

@@ -187,6 +187,43 @@ def test_ftlm_every_kernel_variant(shape):
             F.tune_shape(s, 8, dt, -1)
 
 
+@pytest.mark.parametrize("shape", [(3, 1, 1, 3), (4, 1, 2, 3), (3, 1, 4, 4), (4, 1, 1, 4), (3, 1, 1, 5), (4, 1, 2, 5)])
+def test_ftlm_vector_major_matches_oracle(shape, rng):
+    """Vector-major Lanczos block (each vector contiguous; a warp owns 32
+    consecutive rows, a thread a cube above them), in one pass or in passes
+    whose cubes cover bits [5, n) (the last cube overlapping the one before):
+    random start with a vector offset, basis start and a user block
+    (transposed on the device) against the oracle step by step (complex128)
+    and in the thermodynamics (complex64), on 4x3 and 4x4 lattices."""
+    for w in (W.square_lattice(4, 3, seed=1), W.square_lattice(4, 4, seed=2)):
+        s = F.System.from_dict(w)
+        d = s.dim
+        try:
+            for R in (6, 3):
+                for dt in ("c128", "c64"):
+                    F.tune_shape(s, R, dt, *shape)
+            g = F.run(s, R=6, M=30, T=T, seed=4, vec_offset=3, dtype="c128")
+            assert g["shape"]["vector_major"] == 1
+            o = oracle.ftlm(osys(w), R=6, M=30, T=T, seed=4, vec_offset=3)
+            compare_tridiag(g, o, 1e-10)
+            g64 = F.run(s, R=6, M=30, T=T, seed=4, vec_offset=3, dtype="c64")
+            assert g64["shape"]["vector_major"] == 1
+            for k in KEYS:
+                assert rel(g64[k], o[k], 1e-3, T >= 0.1) < 1e-4, k
+            g = F.run(s, R=3, M=12, T=T, start="basis", basis_offset=d - 3, dtype="c128")
+            ob = oracle.ftlm(osys(w), R=3, M=12, T=T, start="basis", basis_offset=d - 3)
+            compare_tridiag(g, ob, 1e-10)
+            us = rng.normal(size=(d, 3)) + 1j * rng.normal(size=(d, 3))
+            g = F.run(s, R=3, M=12, T=T, start="user", user_start=to_dev(us, "c128"), dtype="c128")
+            ou = oracle.ftlm(osys(w), R=3, M=12, T=T, start="user", user_start=us)
+            assert g["shape"]["vector_major"] == 1
+            compare_tridiag(g, ou, 1e-10)
+        finally:
+            for R in (6, 3):
+                for dt in ("c128", "c64"):
+                    F.tune_shape(s, R, dt, -1)
+
+
 def test_full_size_lanczos_sample():
     """d = 1,048,576: the first Lanczos steps of one vector against the oracle
     (complex128 to 1e-10, complex64 to 1e-5 relative in alpha and beta)."""
@@ -197,6 +234,14 @@ def test_full_size_lanczos_sample():
     for dt, tol in (("c128", 1e-10), ("c64", 1e-5)):
         g = F.run(s, R=1, M=M, T=T, seed=2, dtype=dt)
         compare_tridiag(g, o, tol)
+        try:  # the vector-major block, one pass and four
+            for mp in (3, 5):
+                F.tune_shape(s, 1, dt, 4, 1, 1, mp)
+                g = F.run(s, R=1, M=M, T=T, seed=2, dtype=dt)
+                assert g["shape"]["vector_major"] == 1 and g["shape"]["passes"] == (1 if mp == 3 else 4)
+                compare_tridiag(g, o, tol)
+        finally:
+            F.tune_shape(s, 1, dt, -1)
 
 
 def test_run_rejects_bad_params():

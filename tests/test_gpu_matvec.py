@@ -54,13 +54,15 @@ def test_apply_h_matches_oracle(name, dtype, R, rng):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("shape", [(0, 1, 2), (2, 1, 1), (2, 5, 4), (3, 10, 2), (4, 2, 1), (4, 10, 8), (3, 3, 2),
-                                   (2, 1, 1, 1), (3, 10, 2, 1), (3, 3, 4, 1), (4, 5, 4, 1), (4, 10, 8, 1)])
+                                   (2, 1, 1, 1), (3, 10, 2, 1), (3, 3, 4, 1), (4, 5, 4, 1), (4, 10, 8, 1),
+                                   (3, 1, 1, 3), (4, 1, 2, 4)])
 def test_apply_h_every_kernel_variant(dtype, shape, rng):
     """General kernel (cube_bits 0) and the spin-1/2 register-cube kernel
     with every cube size, several vector-group widths (incl. groups that do
     not divide R) and tile sizes, in one pass or in ceil(N/K) passes (the
     4x4 lattice with K = 3 has an overlapping last cube),
-    on 4x3 and 4x4 lattices."""
+    on 4x3 and 4x4 lattices.  The vector-major shapes (multipass 3, 4) fall
+    back to the row-major cube kernel for row-major blocks."""
     for w in (W.square_lattice(4, 3, seed=1), W.square_lattice(4, 4, seed=2)):
         s = F.System.from_dict(w)
         d, R = s.dim, 10
