@@ -219,7 +219,7 @@ typedef struct {
   int tile_rows;          /* rows per tile */
   int grid;               /* CTAs per H.v launch */
   int threads;            /* threads per CTA */
-  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..5) */
+  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..7) */
 } ftlm_result;
 
 /*
@@ -284,7 +284,9 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
  *                 three-CTA register budget; 5 = vector-major in
  *                 ceil((n - 5) / cube_bits) launches whose cubes cover bits
  *                 [5, n), so that every pair is a cube, mixed or lane-lane
- *                 pair of one launch.  group_vectors is ignored and
+ *                 pair of one launch (one output block per pass, summed
+ *                 by the step); 6 / 7 = 3 / 5 with one 512-thread CTA per
+ *                 SM instead of two of 256.  group_vectors is ignored and
  *                 tile_cubes counts slabs of 2^(5 + cube_bits) rows per warp.
  *                 ftlm_apply_h on row-major blocks uses the row-major
  *                 register-cube kernel for these shapes.

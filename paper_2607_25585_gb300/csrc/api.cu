@@ -154,6 +154,7 @@ struct HalfPlan {
   int K = 3, Rg = 1, threads = 256, rows_per_tile = 0, grid = 0, nvg = 0, tiles_per_vg = 0;
   size_t smem = 0;
   int stream_rows = 0, stream_tiles_per_vg = 0, stream_grid = 0;  // vector-major streaming launches
+  long long dim = 0;
 };
 
 struct Plan {
@@ -209,25 +210,30 @@ bool make_vm(const ftlm_system* s, int R, int c64, int K, int rows_factor, int m
              HalfPlan& h) {
   const HostSystem& hs = s->hs;
   if (!hs.all_half || K < 3 || K > 4 || hs.n < kVmLaneBits + K || rows_factor < 1) return false;
+  if (hs.dim >= (1ull << 31)) return false;  // 32-bit element indices
   h = HalfPlan();
   h.vm = true;
   h.K = K;
   h.Rg = 1;
   h.passes = multipass ? (hs.n - kVmLaneBits + K - 1) / K : 1;  // cubes cover bits [5, n)
-  h.min_blocks = h.passes > 1 ? 2 : (min_blocks > 2 ? 3 : 2);
+  // 1: one 512-thread CTA per SM; 2 or 3: 256-thread CTAs (3 only in one pass)
+  h.min_blocks = min_blocks == 1 ? 1 : (h.passes > 1 ? 2 : (min_blocks > 2 ? 3 : 2));
   h.real_pm = hs.real_pm ? 1 : 0;
-  h.threads = 256;
+  h.threads = h.min_blocks == 1 ? 512 : 256;
   const long long slab = 1ll << (kVmLaneBits + K);
   long long rows = (long long)(h.threads / 32) * slab * rows_factor;
   rows = std::min<long long>(rows, (long long)hs.dim);  // dim and rows are powers of two >= slab
   h.rows_per_tile = (int)rows;
   h.nvg = R;
-  h.tiles_per_vg = (int)((long long)hs.dim / rows);
-  const long long ntiles = (long long)h.tiles_per_vg * R;
+  h.dim = (long long)hs.dim;
+  h.tiles_per_vg = (int)((long long)hs.dim / rows);  // per vector and pass
+  const long long ntiles = (long long)h.tiles_per_vg * R * h.passes;
   if (ntiles > (1ll << 30)) return false;
-  h.smem = vm_smem_bytes(hs.n, K, h.threads);
+  h.smem = vm_smem_bytes(hs.n, K, h.threads, h.passes, c64);
   if (h.smem > 200 * 1024) return false;
   if (prepare_vm_kernels(std::max<size_t>(h.smem, 48 * 1024)) != 0) return false;
+  // the register budget allows min_blocks CTAs per SM: keep only their shared memory, the rest is L1
+  if (set_vm_carveout(K, c64, h.passes > 1, h.min_blocks, h.smem, h.min_blocks) != 0) return false;
   const int per_sm = vm_max_ctas_per_sm(K, h.min_blocks, c64, h.threads, h.smem, h.passes > 1);
   const long long sms = std::max(1, device_sm_count());
   h.grid = (int)std::max<long long>(1, std::min<long long>(ntiles, sms * per_sm));
@@ -301,12 +307,9 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   }
   if (sys.size() == 1 && allow_vm && !force && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
     // default for runs on spin-1/2 systems: the vector-major single-pass gather
-    const int K = c64 ? 4 : 3;  // complex128 cubes of 16 rows spill at the 2-CTA register budget
-    Shape vm = pl.sh;
-    vm.half_K = K;
-    vm.half_rows = 2;
-    vm.half_vm = 1;
-    if (make_vm(sys[0], R, c64, K, 2, 2, false, pl.half)) {
+    const int K = c64 ? 4 : 3;  // complex128 cubes of 16 rows spill at 128 registers
+    // one 512-thread CTA per SM (one copy of the tables, more L1), tiles of 2 units per warp
+    if (make_vm(sys[0], R, c64, K, 2, 1, false, pl.half)) {
       pl.sh = default_shape(1, c64);
       ftlm_status gs = make_general(std::vector<ftlm_system*>(R, sys[0]), 1, c64, pl);
       pl.sh.half_K = K;
@@ -344,21 +347,11 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.real_pm = pl.half.real_pm;
     a.min_blocks = pl.half.min_blocks;
     a.inline_one = 0;
-    if (pl.half.passes == 1) {
-      a.single_pass = 1;
-      return launch_vm(a, pl.half.K, pl.half.min_blocks, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
-    }
-    const int K = pl.half.K, n = pl.base.max_n, ga = a.gather_alpha;
-    for (int p = 0; p < pl.half.passes; ++p) {  // cubes [min(5 + pK, n - K), +K) cover bits [5, n)
-      a.cube_lo = std::min(kVmLaneBits + p * K, n - K);
-      a.new_lo = kVmLaneBits + p * K;
-      a.first_pass = p == 0;
-      a.single_pass = 0;
-      a.gather_alpha = p == pl.half.passes - 1 ? ga : 0;  // alpha from the complete H q_j
-      const int e = launch_vm(a, K, 2, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
-      if (e) return e;
-    }
-    return 0;
+    a.single_pass = pl.half.passes == 1 ? 1 : 0;
+    a.npass = pl.half.passes;  // pass p writes y + p * R * d (vector-major blocks)
+    a.pass_stride = (long long)pl.half.nvg * pl.half.dim;
+    a.ntiles = pl.half.tiles_per_vg * pl.half.nvg * pl.half.passes;
+    return launch_vm(a, pl.half.K, pl.half.min_blocks, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
   }
   const bool half = pl.half.on && !pl.half.vm &&
                     (a.mode == kModeApply || (a.mode == kModeLanczos && pl.half.passes == 1));
@@ -421,8 +414,9 @@ ftlm_status ensure_workspace(ftlm_system* s, int R, int M, int c64) {
   return FTLM_OK;
 }
 
-ftlm_status ensure_hq(ftlm_system* s, int R, int c64) {
-  const size_t block = (size_t)s->hs.dim * R * (c64 ? 8 : 16);
+// parts: H q_j blocks (one per pass of the vector-major multi-pass gather)
+ftlm_status ensure_hq(ftlm_system* s, int R, int c64, int parts = 1) {
+  const size_t block = (size_t)s->hs.dim * R * (c64 ? 8 : 16) * parts;
   if (s->Hq.bytes < block) {
     s->Hq.release();
     CK(s->Hq.ensure(block));
@@ -611,7 +605,10 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
       if (fused) {
         a.mode = kModeStep;
+        a.hq_parts = pl.half.vm ? pl.half.passes : 1;  // the passes' partial H q_j blocks
+        a.hq_stride = (long long)R * (long long)sys[0]->hs.dim;
         CKI(launch_plan(pl, a, st));
+        a.hq_parts = 1;
         ctx.launches += 2;
         ctx.hv_launches++;
         continue;
@@ -729,7 +726,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   ftlm_status ps = make_plan(sys, R, c64, pl, nullptr, true);
   if (ps != FTLM_OK) return ps;
   if (pl.half.on) {
-    ftlm_status hs_ = ensure_hq(sys[0], R, c64);
+    ftlm_status hs_ = ensure_hq(sys[0], R, c64, pl.half.vm ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
   }
   const std::string key = run_key(sys, p, pl);
@@ -845,15 +842,17 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
             }
     for (int mp : {0, 1})  // the vector-major gather (runs only)
       for (int K : {3, 4})
-        for (int f : {1, 2, 4}) {
-          Shape sh = default_shape(R, c64);
-          sh.half_K = K;
-          sh.Rg = largest_divisor_at_most(R, 16);
-          sh.half_rows = f;
-          sh.half_multipass = mp;
-          sh.half_vm = 1;
-          if (s->hs.n >= kVmLaneBits + K) cands.push_back(sh);
-        }
+        for (int f : {1, 2, 4, 8})
+          for (int mb : {1, 2}) {  // one 512-thread or two 256-thread CTAs per SM
+            Shape sh = default_shape(R, c64);
+            sh.half_K = K;
+            sh.Rg = largest_divisor_at_most(R, 16);
+            sh.half_rows = f;
+            sh.half_multipass = mp;
+            sh.half_min_blocks = mb;
+            sh.half_vm = 1;
+            if (s->hs.n >= kVmLaneBits + K) cands.push_back(sh);
+          }
   } else {
     for (int thr : {128, 256})
       for (int f : {1, 4}) cands.push_back(shape_for(R, c64, thr, f));
@@ -862,12 +861,14 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
   if (w != FTLM_OK) return w;
   const size_t vbytes = (size_t)s->hs.dim * (c64 ? 8 : 16);
   CK(cudaMemsetAsync(s->A.p, 0, vbytes * R, st));
-  DevBuf vdesc;  // the vector-major candidates: one descriptor per vector
-  {
+  DevBuf vdesc;  // the vector-major candidates: one descriptor per vector, output in Hq (one block per pass)
+  if (s->hs.all_half && s->hs.n >= kVmLaneBits + 3) {
+    ftlm_status hq = ensure_hq(s, R, c64, (s->hs.n - kVmLaneBits + 2) / 3);  // the most passes a candidate uses
+    if (hq != FTLM_OK) return hq;
     std::vector<InstDesc> h(R, base_desc(s, c64));
     for (int k = 0; k < R; ++k) {
       h[k].x = static_cast<char*>(s->A.p) + vbytes * k;
-      h[k].y = static_cast<char*>(s->B.p) + vbytes * k;
+      h[k].y = static_cast<char*>(s->Hq.p) + vbytes * k;
     }
     CK(vdesc.ensure(sizeof(InstDesc) * R));
     CK(cudaMemcpy(vdesc.p, h.data(), sizeof(InstDesc) * R, cudaMemcpyHostToDevice));
@@ -1197,7 +1198,7 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     if (!s->hs.all_half) return fail(FTLM_ERR_UNSUPPORTED, "register cubes need every site s = 1/2");
     if (cube_bits < 2 || cube_bits > 4 || s->hs.n < cube_bits + 2)
       return fail(FTLM_ERR_INVALID_ARG, "cube_bits must be 2..4 and at most n_sites - 2");
-    if (multipass < 0 || multipass > 5) return fail(FTLM_ERR_INVALID_ARG, "multipass must be in 0..5");
+    if (multipass < 0 || multipass > 7) return fail(FTLM_ERR_INVALID_ARG, "multipass must be in 0..7");
     if (multipass >= 3 && (cube_bits < 3 || s->hs.n < kVmLaneBits + cube_bits))
       return fail(FTLM_ERR_INVALID_ARG, "the vector-major kernel needs cube_bits 3..4 and n_sites >= 5 + cube_bits");
     if (multipass < 3 && (group_vectors < 1 || group_vectors > nvec || group_vectors > 256))
@@ -1206,8 +1207,9 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     sh.half_K = cube_bits;
     sh.Rg = multipass >= 3 ? largest_divisor_at_most(nvec, 16) : group_vectors;  // row-major fallback for apply_h
     sh.half_rows = tile_cubes;
-    sh.half_multipass = (multipass == 1 || multipass == 5) ? 1 : 0;
-    sh.half_min_blocks = (multipass == 2 || multipass == 4) ? 3 : 2;  // 2 and 4: 3-CTA register budget
+    sh.half_multipass = (multipass == 1 || multipass == 5 || multipass == 7) ? 1 : 0;
+    // 2 and 4: 3-CTA register budget; 6 and 7: one 512-thread CTA per SM
+    sh.half_min_blocks = (multipass == 2 || multipass == 4) ? 3 : (multipass >= 6 ? 1 : 2);
     sh.half_vm = multipass >= 3 ? 1 : 0;
   }
   std::lock_guard<std::mutex> lk(g_mu);

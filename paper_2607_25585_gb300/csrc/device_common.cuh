@@ -119,6 +119,15 @@ __device__ __forceinline__ void elementwise_item(const InstDesc& d, const Launch
   } else if (MODE == kModeStep) {  // w = sigma hq - bsp q_{j-1} - alpha sigma q_j; partials |w|^2, p
     real ar[V], ai[V], xr[V], xi[V], qr[V], qi[V], ur[V], ui[V];
     VecIO<real, V>::ldg(d.hq, idx, ar, ai);
+    for (int part = 1; part < a.hq_parts; ++part) {  // the passes' partial sums, in pass order
+      real br[V], bi[V];
+      VecIO<real, V>::ldg(d.hq, idx + part * a.hq_stride, br, bi);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        ar[v] += br[v];
+        ai[v] += bi[v];
+      }
+    }
     VecIO<real, V>::ldg(d.x, idx, xr, xi);
     VecIO<real, V>::ldg(d.u, idx, ur, ui);
     if (!a.first) {

@@ -146,6 +146,13 @@ struct LaunchArgs {
   // kModeApply of the spin-1/2 kernels: also sum Re<x|y> per vector, and the
   // last CTA sets alpha_j = sigma_j^2 Re<q_j|H q_j> (x = q_j, y = H q_j)
   int gather_alpha = 0;
+  // vector-major multi-pass gather: all npass passes in one launch, pass p
+  // writing its partial H x to y + p * pass_stride (complex elements)
+  int npass = 1;
+  long long pass_stride = 0;
+  // kModeStep / kModeEpilogue: H q_j = sum of hq_parts blocks hq + p * hq_stride
+  int hq_parts = 1;
+  long long hq_stride = 0;
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -185,10 +192,12 @@ int prepare_half_kernels(size_t smem);
 int half_max_ctas_per_sm(int K, int c64, int threads, size_t smem, int min_blocks, bool multipass, int R);
 
 // Vector-major spin-1/2 kernel (hv_vm.cu): mode kModeApply over R instances,
-// one per vector (a.tiles_per_vg tiles each), all of one system; K = 3 or 4;
-// a.single_pass = 0: one pass of the multi-pass form (cube_lo, new_lo, first_pass).
+// one per vector, all of one system; K = 3 or 4.  a.single_pass = 1: one pass
+// (a.tiles_per_vg tiles per vector); 0: a.npass passes in the same launch
+// (a.tiles_per_vg tiles per vector and pass, outputs a.pass_stride apart).
 int launch_vm(const LaunchArgs& a, int K, int min_blocks, int c64, int grid, int threads, size_t smem, void* stream);
-size_t vm_smem_bytes(int n, int K, int threads);
+size_t vm_smem_bytes(int n, int K, int threads, int npass, int c64);
+int set_vm_carveout(int K, int c64, bool multipass, int min_blocks, size_t smem, int ctas);
 int prepare_vm_kernels(size_t smem);
 int vm_max_ctas_per_sm(int K, int min_blocks, int c64, int threads, size_t smem, bool multipass);
 // kModeStep / kModeStartNorm over the same one-vector instances (256 threads)

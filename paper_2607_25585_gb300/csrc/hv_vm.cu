@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "device_common.cuh"
@@ -33,28 +35,45 @@ namespace {
 
 constexpr int kLaneBits = kVmLaneBits;
 
+// x[base + r * 2^s0]: in the single-pass form (s0 = 5 at compile time) a
+// 64-bit base with constant offsets; in the multi-pass form (s0 from the pass)
+// 32-bit element indices (the vector-major kernels require d < 2^31)
+template <typename real, bool MP>
+__device__ __forceinline__ typename Cx<real>::v2 ldx_cube(const void* x, long long base, int r, int s0) {
+  using v2 = typename Cx<real>::v2;
+  if (MP) return __ldg(reinterpret_cast<const v2*>(x) + ((unsigned)base + ((unsigned)r << s0)));
+  return __ldg(reinterpret_cast<const v2*>(x) + base + ((long long)r << s0));
+}
+
 template <typename real>
 struct VmSmem {
   real* cp;   // [npairs][4][2] pair coefficients by (bit_i, bit_j) of the row
+  real* cpl;  // the same with the pairs of the last pass's overlap bits zeroed (multi-pass)
   real* fl;   // [n][32][2]  sum_{i < 5} rho_ji m_i(lane)
-  real* fc;   // [n][NR][2]  sum_c rho_{j, 5+c} m_c(r)
+  real* fc;   // [npass][n][NR][2]  sum_c rho_{j, s0(p)+c} m_c(r), cube of pass p
   real* el;   // [32]        diagonal from the lane bits alone
   real* gl;   // [K][32]     sum_{i < 5} zz_{i, 5+c} m_i(lane)
-  real* ec;   // [NR]        diagonal from the cube bits alone
+  real* ec;   // [NR]        diagonal from the cube bits alone (first pass)
   real* ws;   // per warp: fs [n][2], hs [5], gs [K], es [1]
 };
 
 template <typename real>
-__device__ VmSmem<real> vm_carve(unsigned char* raw, int n, int K, int nwarps, int& warp_stride) {
+__device__ VmSmem<real> vm_carve(unsigned char* raw, int n, int K, int npass, int& warp_stride) {
   VmSmem<real> s;
   const int NR = 1 << K;
+  const int npairs = n * (n - 1) / 2;
   real* p = reinterpret_cast<real*>(raw);
   s.cp = p;
-  p += (n * (n - 1) / 2) * 8;
+  p += npairs * 8;
+  s.cpl = s.cp;
+  if (npass > 1) {  // the last pass's table with the overlap bits zeroed
+    s.cpl = p;
+    p += npairs * 8;
+  }
   s.fl = p;
   p += n * 32 * 2;
   s.fc = p;
-  p += n * NR * 2;
+  p += npass * n * NR * 2;
   s.el = p;
   p += 32;
   s.gl = p;
@@ -63,7 +82,6 @@ __device__ VmSmem<real> vm_carve(unsigned char* raw, int n, int K, int nwarps, i
   p += NR;
   s.ws = p;
   warp_stride = 2 * n + kLaneBits + K + 1;
-  (void)nwarps;
   return s;
 }
 
@@ -75,27 +93,39 @@ __device__ __forceinline__ real zzc(const real* t, const TabLayout& L, int n, in
 
 }  // namespace
 
-size_t vm_smem_bytes(int n, int K, int threads) {
+// Dynamic shared memory of vm_kernel (tables of `real`: 4 bytes for
+// complex64, 8 for complex128).  Kept small: the rest of the SM's 256 KB of
+// L1/shared memory is L1 cache, which serves most gathered loads.
+size_t vm_smem_bytes(int n, int K, int threads, int npass, int c64) {
   const int NR = 1 << K, nwarps = threads / 32;
-  const size_t reals = (size_t)(n * (n - 1) / 2) * 8 + (size_t)n * 32 * 2 + (size_t)n * NR * 2 + 32 + (size_t)K * 32 + NR +
+  const size_t reals = (size_t)(n * (n - 1) / 2) * 8 * (npass > 1 ? 2 : 1) + (size_t)n * 32 * 2 +
+                       (size_t)npass * n * NR * 2 + 32 + (size_t)K * 32 + NR +
                        (size_t)nwarps * (2 * n + kLaneBits + K + 1);
-  return reals * 8;  // sized for double tables
+  return reals * (c64 ? 4 : 8);
 }
 
-// MP: one pass of the multi-pass form.  The cube spans bits [a.cube_lo,
-// a.cube_lo + K) (>= 5); cube bits >= a.new_lo are the pass's own: their single
-// flips, their pairs with each other and their mixed pairs with the lane bits
-// and with the bits above the cube.  The first pass (cube on bits [5, 5 + K))
-// also does the diagonal, the lane bits' single flips and the lane-lane pairs
-// and writes the output; later passes add to it.  With ceil((n - 5) / K) passes
-// whose cubes cover bits [5, n), every pair is a cube pair, a mixed pair or a
-// lane-lane pair of exactly one pass, so each gathered load serves K (or K + 1)
-// multiply-adds per row instead of one.
+// Cube of pass p of the multi-pass form: bits [s0, s0 + K) with s0 = min(5 + pK, n - K);
+// its own bits start at 5 + pK (the last cube may overlap the one before).
+__device__ __forceinline__ int vm_pass_lo(int p, int K, int n) { return min(kLaneBits + p * K, n - K); }
+
+// MP: the multi-pass form, all a.npass passes in this launch.  Pass p's cube
+// spans bits [s0, s0 + K), s0 = min(5 + pK, n - K); its cube bits >= 5 + pK
+// are its own: their single flips, their pairs with each other and their
+// mixed pairs with the lane bits and with the bits above the cube.  Pass 0
+// (cube on bits [5, 5 + K)) also does the diagonal, the lane bits' single
+// flips and the lane-lane pairs.  Every pair is then a cube pair, a mixed
+// pair or a lane-lane pair of exactly one pass, so each gathered load serves
+// K (or K + 1) multiply-adds per row instead of one.  Pass p writes its
+// partial H x to y + p * a.pass_stride; the consumer adds the a.npass blocks in
+// pass order.  Tiles run vector by vector, the passes of a vector side by side,
+// so a vector's x is read from HBM once and then served from L2.
 // Without MP: one pass, cube on bits [5, 5 + K), every term; pairs of two bits
 // outside the cube cost one gathered load per multiply-add.
-// MINB: resident CTAs per SM the register allocator must allow.
+// MINB: resident CTAs per SM the register allocator must allow: 2 or 3 CTAs
+// of 256 threads, or 1 = one CTA of 512 threads (the same registers per
+// thread as 2; one copy of the tables per SM leaves more of it to L1).
 template <typename real, int K, bool MP, int MINB>
-__global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ LaunchArgs a) {
+__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const __grid_constant__ LaunchArgs a) {
   using v2 = typename Cx<real>::v2;
   constexpr int NR = 1 << K;
   constexpr int CB = kLaneBits;  // lane bits [0, CB)
@@ -109,18 +139,15 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
   if (threadIdx.x == 0) d = insts[0];
   __syncthreads();
   const int n = d.n;
-  const int s0 = MP ? a.cube_lo : CB;          // cube bits [s0, s0 + K)
-  const int cnew = MP ? a.new_lo - s0 : 0;     // first own cube bit (cube-relative)
-  const bool first = MP ? a.first_pass != 0 : true;
+  const int P = MP ? a.npass : 1;
   int wstride = 0;
-  const VmSmem<real> S = vm_carve<real>(smem_raw, n, K, nwarps, wstride);
+  const VmSmem<real> S = vm_carve<real>(smem_raw, n, K, P, wstride);
   const real* t = reinterpret_cast<const real*>(d.tab);  // every instance of the launch shares the system
   const TabLayout& L = d.lay;
   const int bd = blockDim.x;
-  auto in_cube = [&](int i) { return i >= s0 && i < s0 + K; };
-  // cube bits below new_lo (the overlap of the last pass with the one before)
-  // belong to an earlier pass: their terms get zero coefficients here
-  auto done = [&](int i) { return MP && i >= s0 && i < s0 + cnew; };
+  // the last pass's cube bits below its own bits (overlap with the pass before)
+  const int ov_lo = vm_pass_lo(P - 1, K, n), ov_hi = MP ? CB + (P - 1) * K : ov_lo;
+  auto overlap = [&](int i) { return i >= ov_lo && i < ov_hi; };
 
   // ---- per-system tables ----
   for (int q = threadIdx.x; q < n * n; q += bd) {
@@ -130,16 +157,18 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
     const real pmr = t[L.off_pm + 2 * ij], pmi = t[L.off_pm + 2 * ij + 1];
     const real ppr = t[L.off_pp + 2 * ij], ppi = t[L.off_pp + 2 * ij + 1];
     real* c = S.cp + tri(i, j) * 8;
-    const real z = (done(i) || done(j)) ? (real)0 : (real)1;
-    c[0] = z * ppr; c[1] = -z * ppi;   // (0,0): mu = s-_i s-_j nu
-    c[2] = z * pmr; c[3] = -z * pmi;   // (0,1): mu = s-_i s+_j nu
-    c[4] = z * pmr; c[5] = z * pmi;    // (1,0): mu = s+_i s-_j nu
-    c[6] = z * ppr; c[7] = z * ppi;    // (1,1): mu = s+_i s+_j nu
+    c[0] = ppr; c[1] = -ppi;   // (0,0): mu = s-_i s-_j nu
+    c[2] = pmr; c[3] = -pmi;   // (0,1): mu = s-_i s+_j nu
+    c[4] = pmr; c[5] = pmi;    // (1,0): mu = s+_i s-_j nu
+    c[6] = ppr; c[7] = ppi;    // (1,1): mu = s+_i s+_j nu
+    real* cl = S.cpl + tri(i, j) * 8;
+    const real z = (overlap(i) || overlap(j)) ? (real)0 : (real)1;
+    for (int k = 0; k < 8; ++k) cl[k] = z * c[k];
   }
   for (int q = threadIdx.x; q < n * 32; q += bd) {  // lane part of F_j
     const int j = q / 32, l = q % 32;
     real fr = 0, fi = 0;
-    for (int i = 0; i < CB && !done(j); ++i) {
+    for (int i = 0; i < CB; ++i) {
       const real mi = ((l >> i) & 1) ? (real)0.5 : (real)-0.5;
       fr += t[L.off_rho + 2 * (j * n + i)] * mi;
       fi += t[L.off_rho + 2 * (j * n + i) + 1] * mi;
@@ -147,44 +176,45 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
     S.fl[2 * q] = fr;
     S.fl[2 * q + 1] = fi;
   }
-  for (int q = threadIdx.x; q < n * NR; q += bd) {  // cube part of F_j
-    const int j = q / NR, r = q % NR;
+  for (int q = threadIdx.x; q < P * n * NR; q += bd) {  // cube part of F_j, per pass
+    const int pp = q / (n * NR), j = (q / NR) % n, r = q % NR;
+    const int c0 = vm_pass_lo(pp, K, n);
     real fr = 0, fi = 0;
-    for (int c = 0; c < K && !done(j); ++c) {
-      const real mc = ((r >> c) & 1) ? (real)0.5 : (real)-0.5;
-      fr += t[L.off_rho + 2 * (j * n + s0 + c)] * mc;
-      fi += t[L.off_rho + 2 * (j * n + s0 + c) + 1] * mc;
+    if (!(pp == P - 1 && overlap(j))) {
+      for (int c = 0; c < K; ++c) {
+        const real mc = ((r >> c) & 1) ? (real)0.5 : (real)-0.5;
+        fr += t[L.off_rho + 2 * (j * n + c0 + c)] * mc;
+        fi += t[L.off_rho + 2 * (j * n + c0 + c) + 1] * mc;
+      }
     }
     S.fc[2 * q] = fr;
     S.fc[2 * q + 1] = fi;
   }
-  if (first) {
-    for (int l = threadIdx.x; l < 32; l += bd) {  // lane bits: diagonal and cross terms with the cube
-      real e = 0;
-      for (int i = 0; i < CB; ++i) {
-        const int bi = (l >> i) & 1;
-        const real mi = bi ? (real)0.5 : (real)-0.5;
-        e += t[L.off_hz + i] * mi + t[L.off_iondiag + i * L.qmax + bi];
-        for (int i2 = i + 1; i2 < CB; ++i2) e += zzc(t, L, n, i, i2) * mi * (((l >> i2) & 1) ? (real)0.5 : (real)-0.5);
-      }
-      S.el[l] = e;
-      for (int c = 0; c < K; ++c) {
-        real g = 0;
-        for (int i = 0; i < CB; ++i) g += zzc(t, L, n, i, s0 + c) * (((l >> i) & 1) ? (real)0.5 : (real)-0.5);
-        S.gl[c * 32 + l] = g;
-      }
+  for (int l = threadIdx.x; l < 32; l += bd) {  // lane bits: diagonal and cross terms with the first cube
+    real e = 0;
+    for (int i = 0; i < CB; ++i) {
+      const int bi = (l >> i) & 1;
+      const real mi = bi ? (real)0.5 : (real)-0.5;
+      e += t[L.off_hz + i] * mi + t[L.off_iondiag + i * L.qmax + bi];
+      for (int i2 = i + 1; i2 < CB; ++i2) e += zzc(t, L, n, i, i2) * mi * (((l >> i2) & 1) ? (real)0.5 : (real)-0.5);
     }
-    for (int r = threadIdx.x; r < NR; r += bd) {  // cube bits alone
-      real e = 0;
-      for (int c = 0; c < K; ++c) {
-        const int bc = (r >> c) & 1;
-        const real mc = bc ? (real)0.5 : (real)-0.5;
-        e += t[L.off_hz + s0 + c] * mc + t[L.off_iondiag + (s0 + c) * L.qmax + bc];
-        for (int c2 = c + 1; c2 < K; ++c2)
-          e += zzc(t, L, n, s0 + c, s0 + c2) * mc * (((r >> c2) & 1) ? (real)0.5 : (real)-0.5);
-      }
-      S.ec[r] = e;
+    S.el[l] = e;
+    for (int c = 0; c < K; ++c) {
+      real g = 0;
+      for (int i = 0; i < CB; ++i) g += zzc(t, L, n, i, CB + c) * (((l >> i) & 1) ? (real)0.5 : (real)-0.5);
+      S.gl[c * 32 + l] = g;
     }
+  }
+  for (int r = threadIdx.x; r < NR; r += bd) {  // first cube's bits alone
+    real e = 0;
+    for (int c = 0; c < K; ++c) {
+      const int bc = (r >> c) & 1;
+      const real mc = bc ? (real)0.5 : (real)-0.5;
+      e += t[L.off_hz + CB + c] * mc + t[L.off_iondiag + (CB + c) * L.qmax + bc];
+      for (int c2 = c + 1; c2 < K; ++c2)
+        e += zzc(t, L, n, CB + c, CB + c2) * mc * (((r >> c2) & 1) ? (real)0.5 : (real)-0.5);
+    }
+    S.ec[r] = e;
   }
   __syncthreads();
 
@@ -196,8 +226,6 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
   // a unit: 32 lanes x the cube = 2^(5+K) rows whose other ("outer") bits are fixed
   const long long nunits = d.dim >> (CB + K);
   const int units_per_tile = a.rows_per_tile >> (CB + K);
-  const unsigned long long lowmask = (1ull << (s0 - CB)) - 1ull;  // outer bits between the lanes and the cube
-  const int nnb = CB + n - s0 - K;  // neighbour bits: the lane bits and the bits above the cube
   const bool real_fast_pm = a.real_pm != 0;
   if (kPartials)  // this CTA's slot of every vector: [vector][CTA][kNumPartials]
     for (int k = threadIdx.x; k < a.n_inst * kNumPartials; k += bd)
@@ -218,17 +246,29 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
   double adot = 0.0;
   int cur = -1;
   const void* x = nullptr;
-  void* y = nullptr;
+  void* y0 = nullptr;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int inst = tile / a.tiles_per_vg;  // tiles are vector-major: every vector has tiles_per_vg of them
+    // tiles: [vector][pass][tile of the pass]
+    const int inst = tile / (P * a.tiles_per_vg);
+    const int pass = MP ? (tile / a.tiles_per_vg) % P : 0;
+    const int ptile = tile % a.tiles_per_vg;
     if (inst != cur) {  // per-vector pointers (the tables are shared)
       if (kPartials && cur >= 0) flush(cur, adot);
       adot = 0.0;
       x = insts[inst].x;
-      y = insts[inst].y;
+      y0 = insts[inst].y;
       cur = inst;
     }
-    const long long unit0 = (long long)(tile - inst * a.tiles_per_vg) * units_per_tile;
+    const int s0 = MP ? vm_pass_lo(pass, K, n) : CB;         // cube bits [s0, s0 + K)
+    const int cnew = MP ? CB + pass * K - s0 : 0;            // first own cube bit (cube-relative)
+    const bool first = !MP || pass == 0;
+    const real* cpb = (MP && pass == P - 1) ? S.cpl : S.cp;  // overlap pairs zeroed in the last pass
+    const real* fcp = S.fc + (size_t)pass * n * NR * 2;
+    v2* const y = reinterpret_cast<v2*>(y0) + (MP ? pass * a.pass_stride : 0);
+    const unsigned long long lowmask = (1ull << (s0 - CB)) - 1ull;  // outer bits between the lanes and the cube
+    const int nnb = CB + n - s0 - K;  // neighbour bits: the lane bits and the bits above the cube
+    auto in_cube = [&](int i) { return i >= s0 && i < s0 + K; };
+    const long long unit0 = (long long)ptile * units_per_tile;
     for (int ui = warp; ui < units_per_tile; ui += nwarps) {
       const unsigned long long u = (unsigned long long)(unit0 + ui);
       if ((long long)u >= nunits) break;
@@ -236,9 +276,8 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
       // unit tables (the outer bits' share of the coefficients), the warp's lanes in parallel
       __syncwarp();
       for (int j = lane; j < n; j += 32) {
-        const real z = done(j) ? (real)0 : (real)1;
-        real fr = z * t[L.off_hp + 2 * j], fi = z * t[L.off_hp + 2 * j + 1];
-        for (int i = CB; i < n && !done(j); ++i) {
+        real fr = t[L.off_hp + 2 * j], fi = t[L.off_hp + 2 * j + 1];
+        for (int i = CB; i < n; ++i) {
           if (in_cube(i)) continue;
           const real mi = ((base >> i) & 1ull) ? (real)0.5 : (real)-0.5;
           fr += t[L.off_rho + 2 * (j * n + i)] * mi;
@@ -277,14 +316,10 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
       }
       __syncwarp();
       const long long row0 = (long long)(base | (unsigned long long)lane);
-      if (!first)  // the earlier passes' sums are read at the end of the unit: bring them to L2 now
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const v2*>(y) + row0 + ((long long)r << s0)));
       v2 xo[NR];
       Cx<real> acc[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) xo[r] = ldx<real>(x, row0 + ((long long)r << s0));
+      for (int r = 0; r < NR; ++r) xo[r] = ldx_cube<real, MP>(x, row0, r, s0);
       if (first) {  // diagonal
         real eo = S.el[lane] + es[0];
 #pragma unroll
@@ -303,20 +338,23 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r].set((real)0, xo[r]);
       }
-      // own cube bits: single flips and pairs in registers
+      // own cube bits: single flips and pairs in registers (an overlap bit of the
+      // last pass has zero coefficients)
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         const int sc = s0 + c;
-        const real br = fs[2 * sc] + S.fl[2 * (sc * 32 + lane)], bi = fs[2 * sc + 1] + S.fl[2 * (sc * 32 + lane) + 1];
+        const real om = (MP && c < cnew) ? (real)0 : (real)1;
+        const real br = om * (fs[2 * sc] + S.fl[2 * (sc * 32 + lane)]);
+        const real bi = om * (fs[2 * sc + 1] + S.fl[2 * (sc * 32 + lane) + 1]);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          const real fr = br + S.fc[2 * (sc * NR + r)];
-          const real fim = bi + S.fc[2 * (sc * NR + r) + 1];
+          const real fr = br + fcp[2 * (sc * NR + r)];
+          const real fim = bi + fcp[2 * (sc * NR + r) + 1];
           acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
         }
 #pragma unroll
         for (int c1 = 0; c1 < c; ++c1) {
-          const real* cp = S.cp + tri(s0 + c1, sc) * 8;
+          const real* cp = cpb + tri(s0 + c1, sc) * 8;
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             const int idx = 2 * ((r >> c1) & 1) + ((r >> c) & 1);
@@ -333,21 +371,13 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
         const long long nb = row0 ^ (1ll << j);
         v2 yv[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) yv[r] = ldx<real>(x, nb + ((long long)r << s0));
-        if (MP && jj + 1 < nnb) {  // the next neighbour cube to L1 while this one is used
-          const int jn = jj + 1 < CB ? jj + 1 : s0 + K + (jj + 1 - CB);
-          if (jn >= CB) {  // (the lane-bit neighbours share the own rows' lines)
-            const v2* nx = reinterpret_cast<const v2*>(x) + (row0 ^ (1ll << jn));
-#pragma unroll
-            for (int r = 0; r < NR; ++r) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + ((long long)r << s0)));
-          }
-        }
+        for (int r = 0; r < NR; ++r) yv[r] = ldx_cube<real, MP>(x, nb, r, s0);
         if (!MP || (first && j < CB)) {
           const real br = fs[2 * j] + S.fl[2 * (j * 32 + lane)], bi = fs[2 * j + 1] + S.fl[2 * (j * 32 + lane) + 1];
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            const real fim = bi + S.fc[2 * (j * NR + r) + 1];
-            acc[r].mac(br + S.fc[2 * (j * NR + r)], bj ? fim : -fim, yv[r]);
+            const real fim = bi + fcp[2 * (j * NR + r) + 1];
+            acc[r].mac(br + fcp[2 * (j * NR + r)], bj ? fim : -fim, yv[r]);
           }
         }
         const bool uniform = j >= CB;  // bit j (above the cube) is the same for the whole warp
@@ -355,7 +385,7 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
         for (int c = 0; c < K; ++c) {
           const int sc = s0 + c;
           // pair (min, max) and the row's bits in that order
-          const real* cp = S.cp + (j < sc ? tri(j, sc) : tri(sc, j)) * 8;
+          const real* cp = cpb + (j < sc ? tri(j, sc) : tri(sc, j)) * 8;
           if (uniform && real_fast_pm) {
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
@@ -375,7 +405,7 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
         }
       }
       // pairs of two neighbour bits: one coefficient for the whole cube (without
-      // MP every such pair; with MP only the lane-lane pairs, in the first pass)
+      // MP every such pair; with MP only the lane-lane pairs, in pass 0)
       if (first) {
         const int npb = MP ? CB : nnb;
         for (int jj = 1; jj < npb; ++jj) {
@@ -385,12 +415,12 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
           for (int ii = 0; ii < jj; ++ii) {
             const int i = ii < CB ? ii : s0 + K + (ii - CB);
             const int bi = (int)((row0 >> i) & 1);
-            const real* cp = S.cp + tri(i, j) * 8 + 2 * (2 * bi + bj);
+            const real* cp = cpb + tri(i, j) * 8 + 2 * (2 * bi + bj);
             const real cr = cp[0], ci = cp[1];
             const long long nb = row0 ^ (1ll << i) ^ (1ll << j);
             v2 yv[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) yv[r] = ldx<real>(x, nb + ((long long)r << s0));
+            for (int r = 0; r < NR; ++r) yv[r] = ldx_cube<real, MP>(x, nb, r, s0);
             if (i >= CB && real_fast_pm && bi != bj) {  // warp-uniform and real
 #pragma unroll
               for (int r = 0; r < NR; ++r) acc[r].mac_re(cr, yv[r]);
@@ -402,21 +432,12 @@ __global__ void __launch_bounds__(256, MINB) vm_kernel(const __grid_constant__ L
         }
       }
       real pd = 0;
-      v2* const yb = reinterpret_cast<v2*>(y) + row0;
-      if (!first) {  // add the earlier passes' sums: all loads first, then the stores
-        v2 prev[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) prev[r] = __ldcs(yb + ((long long)r << s0));
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r].add(prev[r]);
-      }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        v2* yp = yb + ((long long)r << s0);
         const v2 hv = acc[r].value();
-        __stcs(yp, hv);
+        __stcs(MP ? y + ((unsigned)row0 + ((unsigned)r << s0)) : y + row0 + ((long long)r << s0), hv);
         if (kPartials) {  // the own rows are re-read (L1) rather than kept in registers
-          const v2 xv = ldx<real>(x, row0 + ((long long)r << s0));
+          const v2 xv = ldx_cube<real, MP>(x, row0, r, s0);
           pd += xv.x * hv.x + xv.y * hv.y;
         }
       }
@@ -536,11 +557,26 @@ int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream) {
   return (int)cudaGetLastError();
 }
 
+template <typename real, int K, bool MP>
+static const void* vm_fn(int minb) {
+  if (minb == 1) return (const void*)vm_kernel<real, K, MP, 1>;
+  if (!MP && minb > 2) return (const void*)vm_kernel<real, K, false, 3>;
+  return (const void*)vm_kernel<real, K, MP, 2>;
+}
+
 template <typename real, int K>
 static int launch_vm_k(const LaunchArgs& a, int minb, int grid, int threads, size_t smem, cudaStream_t st) {
-  if (!a.single_pass) vm_kernel<real, K, true, 2><<<grid, threads, smem, st>>>(a);
-  else if (minb > 2) vm_kernel<real, K, false, 3><<<grid, threads, smem, st>>>(a);
-  else vm_kernel<real, K, false, 2><<<grid, threads, smem, st>>>(a);
+  if ((minb == 1) != (threads == 512)) return (int)cudaErrorInvalidValue;
+  if (!a.single_pass) {
+    if (minb == 1) vm_kernel<real, K, true, 1><<<grid, threads, smem, st>>>(a);
+    else vm_kernel<real, K, true, 2><<<grid, threads, smem, st>>>(a);
+  } else if (minb == 1) {
+    vm_kernel<real, K, false, 1><<<grid, threads, smem, st>>>(a);
+  } else if (minb > 2) {
+    vm_kernel<real, K, false, 3><<<grid, threads, smem, st>>>(a);
+  } else {
+    vm_kernel<real, K, false, 2><<<grid, threads, smem, st>>>(a);
+  }
   return (int)cudaGetLastError();
 }
 
@@ -559,9 +595,10 @@ int launch_vm(const LaunchArgs& a, int K, int minb, int c64, int grid, int threa
 
 template <typename real, int K>
 static void vm_variants(std::vector<const void*>& ks) {
-  ks.push_back((const void*)vm_kernel<real, K, false, 2>);
-  ks.push_back((const void*)vm_kernel<real, K, false, 3>);
-  ks.push_back((const void*)vm_kernel<real, K, true, 2>);
+  for (int minb : {1, 2, 3}) {
+    ks.push_back(vm_fn<real, K, false>(minb));
+    ks.push_back(vm_fn<real, K, true>(minb));
+  }
 }
 
 int prepare_vm_kernels(size_t smem) {
@@ -577,11 +614,29 @@ int prepare_vm_kernels(size_t smem) {
   return 0;
 }
 
+// Shared-memory carveout (percent of the SM's L1/shared capacity) for the
+// launch about to run: what `ctas` resident CTAs of `smem` bytes need, so that
+// the remainder stays L1 cache.
+int set_vm_carveout(int K, int c64, bool multipass, int min_blocks, size_t smem, int ctas) {
+  const void* k = nullptr;
+  if (c64) {
+    if (K == 3) k = multipass ? vm_fn<float, 3, true>(min_blocks) : vm_fn<float, 3, false>(min_blocks);
+    if (K == 4) k = multipass ? vm_fn<float, 4, true>(min_blocks) : vm_fn<float, 4, false>(min_blocks);
+  } else {
+    if (K == 3) k = multipass ? vm_fn<double, 3, true>(min_blocks) : vm_fn<double, 3, false>(min_blocks);
+    if (K == 4) k = multipass ? vm_fn<double, 4, true>(min_blocks) : vm_fn<double, 4, false>(min_blocks);
+  }
+  if (!k) return (int)cudaErrorInvalidValue;
+  const double total = 228.0 * 1024.0;  // shared memory per SM
+  const double need = (double)ctas * ((double)smem + 1024.0 + 2048.0);  // + per-CTA reserve and static tables
+  const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / total)));
+  return (int)cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 template <typename real, int K>
 static cudaError_t vm_occ(int* nb, int minb, bool multipass, int threads, size_t smem) {
-  if (multipass) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, vm_kernel<real, K, true, 2>, threads, smem);
-  if (minb > 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, vm_kernel<real, K, false, 3>, threads, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, vm_kernel<real, K, false, 2>, threads, smem);
+  const void* k = multipass ? vm_fn<real, K, true>(minb) : vm_fn<real, K, false>(minb);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k, threads, smem);
 }
 
 int vm_max_ctas_per_sm(int K, int minb, int c64, int threads, size_t smem, bool multipass) {

@@ -187,7 +187,8 @@ def test_ftlm_every_kernel_variant(shape):
             F.tune_shape(s, 8, dt, -1)
 
 
-@pytest.mark.parametrize("shape", [(3, 1, 1, 3), (4, 1, 2, 3), (3, 1, 4, 4), (4, 1, 1, 4), (3, 1, 1, 5), (4, 1, 2, 5)])
+@pytest.mark.parametrize("shape", [(3, 1, 1, 3), (4, 1, 2, 3), (3, 1, 4, 4), (4, 1, 1, 4), (3, 1, 1, 5), (4, 1, 2, 5),
+                                   (4, 1, 1, 6), (3, 1, 2, 7)])
 def test_ftlm_vector_major_matches_oracle(shape, rng):
     """Vector-major Lanczos block (each vector contiguous; a warp owns 32
     consecutive rows, a thread a cube above them), in one pass or in passes
