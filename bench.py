@@ -134,7 +134,7 @@ def run_ours(args):
         F.tune_shape(s, R, "c64", *[int(v) for v in args.shape.split(",")])
         F.run(s, **kw)                     # captures the graph
     else:
-        F.run(s, autotune=True, **kw)      # tunes launch shapes, captures the graph
+        F.run(s, autotune=args.autotune, **kw)  # (tunes launch shapes,) captures the graph
     for _ in range(args.warmup):
         F.run(s, **kw)
     sampler = ClockSampler(local)
@@ -241,15 +241,20 @@ def measured_traffic(shape):
     import hashlib
     tf = os.path.join(ROOT, "profiles", "traffic_lattice4x5.json")
     try:
-        rec = json.load(open(tf))
-        src = open(os.path.join(ROOT, rec["source_file"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
-            return None
-        if any(rec["shape"][k] != shape.get(k) for k in rec["shape"]):
-            return None
-        return rec["bytes_per_launch"]
+        recs = json.load(open(tf))["records"]
     except Exception:
         return None
+    for rec in recs:
+        try:
+            src = open(os.path.join(ROOT, rec["source_file"]), "rb").read()
+        except OSError:
+            continue
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            continue
+        if any(rec["shape"][k] != shape.get(k) for k in rec["shape"]):
+            continue
+        return rec["bytes_per_launch"]
+    return None
 
 
 def plain_fp64(F, s, T, spec, stream, args):
@@ -260,7 +265,7 @@ def plain_fp64(F, s, T, spec, stream, args):
     M = args.M or spec["M"]
     chains = args.plain_chains
     kw = dict(R=1, M=M, T=T, seed=spec["seed"], dtype="c128", stream=stream)
-    F.run(s, autotune=True, **kw)
+    F.run(s, autotune=args.autotune, **kw)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -284,7 +289,7 @@ def extra_workloads(F, T, stream, args):
     systems = [F.System.from_dict(w) for w in spec["system"]()]
     R, M = spec["R"], spec["M"]
     kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True)
-    F.run_batch(systems, autotune=True, **kw)
+    F.run_batch(systems, autotune=args.autotune, **kw)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -302,7 +307,7 @@ def extra_workloads(F, T, stream, args):
     s = F.System.from_dict(spec["system"]())
     R, M = spec["R"], args.ladder_steps
     kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True)
-    F.run(s, autotune=True, **kw)
+    F.run(s, autotune=args.autotune, **kw)
     e0.record(stream)
     res = F.run(s, **kw)
     e1.record(stream)
@@ -363,10 +368,30 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_profile(args):
+    """One short Lanczos run (R vectors, M steps, complex64) of the workload
+    through ftlm_run, with the default plan or --shape: the launches a profiler
+    captures are those of the timed runs, on a case small enough to capture."""
+    import paper_2607_25585_gb300 as F
+
+    F.build()
+    R, M = (int(v) for v in args.profile_run.split(","))
+    spec = W.WORKLOADS[args.hv_workload]
+    w = spec["system"]()
+    if isinstance(w, list):  # a batch: the largest instance
+        w = max(w, key=lambda v: int(np.prod(v["two_s"].astype(np.int64) + 1)))
+    s = F.System.from_dict(w)
+    if args.shape:
+        F.tune_shape(s, R, "c64", *[int(v) for v in args.shape.split(",")])
+    out = F.run(s, R=R, M=M, T=W.temperatures(), seed=spec["seed"], dtype="c64", time_kernels=True)
+    return {"mode": "profile_run", "workload": args.hv_workload, "d": s.dim, "R": R, "M": M,
+            "hv_ms_per_launch": out["hv_ms"] / max(1, out["hv_launches"]), "launch_shape": out["shape"]}
+
+
 def run_hv_only(args):
-    """The dominant kernel alone: args.hv_only launches of H.v on the bench
-    workload's [d][R] complex64 block (the same kernel and launch shape the
-    Lanczos steps use), timed with CUDA events.  Used for ncu captures."""
+    """ftlm_apply_h alone: args.hv_only launches of H.v on the workload's
+    row-major [d][R] complex64 block (the row-major kernels, as a caller of
+    ftlm_apply_h gets them), timed with CUDA events."""
     import torch
 
     import paper_2607_25585_gb300 as F
@@ -413,8 +438,15 @@ def main():
     ap.add_argument("--hv-only", type=int, default=0, help="time N launches of the H.v kernel alone")
     ap.add_argument("--hv-workload", default=WORKLOAD, choices=sorted(W.WORKLOADS),
                     help="workload of --hv-only (a batch uses its largest instance)")
-    ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] instead of autotuning")
+    ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] for the main run")
+    ap.add_argument("--profile-run", default="", help="R,M: one short run of --hv-workload (for profilers)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time candidate launch shapes first (default: the library's default plan, which "
+                         "keeps the command's kernels the same under a profiler)")
     args = ap.parse_args()
+    if args.profile_run:
+        print(json.dumps(run_profile(args)))
+        return
     if args.hv_only:
         print(json.dumps(run_hv_only(args)), flush=True)
         return

@@ -900,6 +900,8 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (pl.half.vm && pl.half.passes > 1)  // the step then reads passes - 1 more H q blocks (~6 TB/s)
+      ms += 5.0f * (float)((double)(pl.half.passes - 1) * (double)vbytes * R / 6.0e9);
     if (ms < best) {
       best = ms;
       pick = sh;
