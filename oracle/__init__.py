@@ -75,6 +75,7 @@ def _load():
         _lib.oracle_pair_tensor.argtypes = [P(_CSystem), i32, i32, pd]
         _lib.oracle_apply_h.argtypes = [P(_CSystem), pd, pd, i64]
         _lib.oracle_apply_sdir.argtypes = [P(_CSystem), pd, pd, pd, i64]
+        _lib.oracle_time_reverse.argtypes = [P(_CSystem), pd, pd, i64]
         _lib.oracle_h_column.restype = i64
         _lib.oracle_h_column.argtypes = [P(_CSystem), i64, P(i64), pd, i64]
         _lib.oracle_philox4x32_10.argtypes = [P(ctypes.c_uint32)] * 3
@@ -227,6 +228,31 @@ def start_vectors(d: int, R: int, seed: int, vec_offset: int = 0) -> np.ndarray:
     return out
 
 
+def time_reverse(sys: System, x: np.ndarray) -> np.ndarray:
+    """Theta x = exp(-i pi S^y) K x for a [d] or [d][R] block (Sec. II.B)."""
+    lib = _load()
+    xx = _cx(x)
+    shape = xx.shape
+    xx = xx.reshape(sys.dim, -1)
+    y = np.empty_like(xx)
+    cs = sys.c()
+    assert lib.oracle_time_reverse(ctypes.byref(cs), _pd(xx.view(np.float64)), _pd(y.view(np.float64)),
+                                   xx.shape[1]) == 0
+    return y.reshape(shape)
+
+
+def start_pairs(sys: System, R: int, seed: int, vec_offset: int = 0) -> np.ndarray:
+    """[d][R] block of time-reversed pairs: global vector v = vec_offset + k is
+    random vector v // 2 (normalised), time-reversed when v is odd."""
+    base = start_vectors(sys.dim, (vec_offset + R + 1) // 2 - vec_offset // 2, seed, vec_offset // 2)
+    out = np.empty((sys.dim, R), dtype=np.complex128)
+    for k in range(R):
+        v = vec_offset + k
+        col = base[:, v // 2 - vec_offset // 2]
+        out[:, k] = time_reverse(sys, col) if v % 2 else col
+    return out
+
+
 def lanczos(sys: System, v0: np.ndarray, M: int, reorth: bool = False, tol: float = 1e-12, direction=None):
     """One Lanczos run; returns (alpha, beta, p, M_eff)."""
     lib = _load()
@@ -286,7 +312,7 @@ def ftlm(sys: System, R: int, M: int, T=None, seed: int = 0, vec_offset: int = 0
     lib = _load()
     T = default_temperatures() if T is None else np.ascontiguousarray(T, dtype=np.float64)
     nT = len(T)
-    mode = {"random": 0, "basis": 1, "user": 2}[start]
+    mode = {"random": 0, "basis": 1, "user": 2, "pairs": 3}[start]
     us = None
     if mode == 2:
         us = _cx(user_start).reshape(sys.dim, R)

@@ -142,3 +142,14 @@ def thermo_from_vectors(sys, T, vecs, direction=None, H=None):
         out["M_B"][t] = -sys.g * np.real(o) / z
         out["M_B_imag"][t] = -sys.g * np.imag(o) / z
     return out
+
+
+def time_reversal_unitary(two_s):
+    """U = (x)_i exp(-i pi s^y_i) (site 0 rightmost), so that the time-reversal
+    operator is Theta x = U conj(x) (Sec. II.B).  Built with scipy's expm of
+    each site's s^y matrix, independently of any closed form."""
+    import scipy.linalg as sla
+    U = np.ones((1, 1), dtype=np.complex128)
+    for t in reversed(list(two_s)):  # site n-1 leftmost
+        U = np.kron(U, sla.expm(-1j * np.pi * spin_matrices(t)[1]))
+    return U

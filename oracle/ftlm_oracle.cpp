@@ -14,7 +14,11 @@
 //   * the Lanczos recurrence with two predecessor vectors and optional full
 //     re-orthogonalisation (Sec. II.C);
 //   * the FTLM estimators Eq. (4) (observable ratio, same r in numerator and
-//     denominator) and Eq. (5) (partition function, Gamma = 1: no symmetry).
+//     denominator) and Eq. (5) (partition function, Gamma = 1: no symmetry);
+//   * pairs of mutually time-reversed random vectors (Sec. II.B: the
+//     time-reversal symmetry used for the FTLM approximation, tau = 1 in the
+//     figures of Sec. III), Theta = exp(-i pi S^y) K with K the complex
+//     conjugation in the S^z product basis.
 //
 // Readings where the paper is silent (each is listed in the design notes):
 //   basis index mu = sum_i a_i * prod_{k<i} q_k, site 0 least significant,
@@ -429,7 +433,27 @@ void jacobi_tridiag(int m, const double* alpha, const double* beta, double* eval
   std::memcpy(evecs, V.data(), sizeof(double) * (size_t)m * m);
 }
 
+// Time reversal Theta = exp(-i pi S^y) K on x (Sec. II.B).  On one site,
+// exp(-i pi s^y)|s, m> = (-1)^(s - m) |s, -m>, so for a product state
+// Theta |mu> = prod_i (-1)^(s_i - m_i) |mu'> with m_i -> -m_i, and the
+// coefficient is conjugated: y[mu'] = prod_i (-1)^(s_i - m_i(mu)) conj(x[mu]).
+void time_reverse(const Model& M, const cplx* x, cplx* y, int64_t nvec) {
+  for (int64_t mu = 0; mu < M.dim; ++mu) {
+    int64_t image = 0;
+    int sign_exp = 0;
+    for (int i = 0; i < M.n; ++i) {
+      const int64_t a = (mu / M.stride[i]) % M.q[i];  // a = m + s
+      const int64_t a_img = M.two_s[i] - a;          // m -> -m
+      image += a_img * M.stride[i];
+      sign_exp += (int)(M.two_s[i] - a);             // s - m = 2s - a
+    }
+    const double ph = (sign_exp % 2) ? -1.0 : 1.0;
+    for (int64_t k = 0; k < nvec; ++k) y[image * nvec + k] = ph * std::conj(x[mu * nvec + k]);
+  }
+}
+
 }  // namespace
+
 
 extern "C" {
 
@@ -462,6 +486,14 @@ int oracle_apply_sdir(const oracle_system* s, const double* dir, const double* x
   Model M;
   if (!build_model(s, M) || nvec <= 0) return -1;
   apply_sdir(M, dir, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y), nvec);
+  return 0;
+}
+
+// y = Theta x (time reversal, Sec. II.B); x, y: [dim][nvec], not aliased.
+int oracle_time_reverse(const oracle_system* s, const double* x, double* y, int64_t nvec) {
+  Model M;
+  if (!build_model(s, M) || nvec <= 0 || x == y) return -1;
+  time_reverse(M, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y), nvec);
   return 0;
 }
 
@@ -615,6 +647,18 @@ int oracle_ftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t
       }
       nrm = std::sqrt(nrm);
       for (auto& z : v0) z /= nrm;
+    } else if (start_mode == 3) {  // time-reversed pairs: vector 2k = r_k, 2k + 1 = Theta r_k
+      const uint64_t v = vec_offset + (uint64_t)r;
+      std::vector<cplx> rk(M.dim);
+      double nrm = 0.0;
+      for (int64_t nu = 0; nu < M.dim; ++nu) {
+        rk[nu] = gaussian_component(seed, v / 2, (uint64_t)nu);
+        nrm += std::norm(rk[nu]);
+      }
+      nrm = std::sqrt(nrm);
+      for (auto& z : rk) z /= nrm;
+      if (v % 2) time_reverse(M, rk.data(), v0.data(), 1);
+      else v0 = rk;
     } else if (start_mode == 1) {
       int64_t b = basis_offset + r;
       if (b < 0 || b >= M.dim) {
