@@ -317,7 +317,75 @@ def extra_workloads(F, T, stream, args):
                          "hv_ms_per_launch": res["hv_ms"] / max(1, res["hv_launches"]), "launch_shape": res["shape"],
                          "note": f"sample of {M} Lanczos steps (the workload runs 300)"}
     s.close()
+    out["time_reversed_pairs"] = time_reversal_leg(F, T, stream)
+    out["mn9_powder"] = mn9_leg(F, T, stream, args)
     return out
+
+
+def mn9_leg(F, T, stream, args):
+    """The mixed-spin Mn9-like system (d = 2,343,750) at 1 T along the 10
+    dodecahedron directions, as one batch (one graph), with time-reversed
+    start pairs; the powder average of M_B is over the 10 results."""
+    import torch
+    spec = W.WORKLOADS["mn9_powder"]
+    systems = [F.System.from_dict(w) for w in spec["system"]()]
+    R, M = spec["R"], spec["M"]
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True, start="pairs")
+    F.run_batch(systems, autotune=args.autotune, **kw)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = F.run_batch(systems, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sv = sum(s.dim for s in systems) * R * M
+    d = int(systems[0].dim)
+    mb = np.mean([r["M_B"] for r in res], axis=0)
+    for s in systems:
+        s.close()
+    return {"value": sv / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R, "directions": len(systems),
+            "d": d, "hv_ms_per_launch": res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
+            "launch_shape": res[0]["shape"], "powder_M_B_at_T": {f"{T[i]:.3g}": float(mb[i]) for i in (0, 20, 39)},
+            "note": "one graph for the 10 directions; general mixed-radix kernel"}
+
+
+def time_reversal_leg(F, T, stream):
+    """Time-reversed start pairs (tau = 1) on the headline system: one FTLM
+    run with pairs (same throughput as random starts: only the start block
+    differs), and ftlm_time_reverse on the [d][R] complex64 block, an
+    HBM-bound permutation (read 8 B + write 8 B per state x vector)."""
+    import torch
+    spec = W.WORKLOADS[WORKLOAD]
+    s = F.System.from_dict(spec["system"]())
+    d, R = s.dim, spec["R"]
+    kw = dict(R=R, M=20, T=T, seed=spec["seed"], dtype="c64", stream=stream, start="pairs")
+    F.run(s, **kw)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    F.run(s, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    run_ms = e0.elapsed_time(e1)
+    x = torch.empty(d, R, dtype=torch.complex64, device="cuda")
+    F.start_pairs(s, x, R, seed=1, dtype="c64", stream=stream)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        F.time_reverse(s, x, y, R, "c64", stream=stream)
+    n = 20
+    e0.record(stream)
+    for _ in range(n):
+        F.time_reverse(s, x, y, R, "c64", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    hbm = load_peaks().get("hbm_gbs", 6778.0)
+    gbs = 2 * d * R * 8 / (ms / 1e3) / 1e9
+    s.close()
+    return {"run_value": d * R * 20 / (run_ms / 1e3), "unit": UNIT, "run_M": 20, "R": R,
+            "time_reverse_ms": ms, "time_reverse_gbs": gbs, "time_reverse_hbm_frac": gbs / hbm,
+            "note": "run: 20 Lanczos steps from 32 pairs; time_reverse: 2 x 8 B per state x vector moved"}
 
 
 def cpu_baseline(args, steps=None):

@@ -22,7 +22,17 @@ Geometry readings (the workload list gives lattice names only):
   lexicographic (i < j) order; random axes: isotropic on the sphere from
   ``default_rng(seed).normal`` normalised;
 * field directions on a Fibonacci sphere: z_k = 1 - (2k+1)/K,
-  phi_k = k pi (3 - sqrt 5).
+  phi_k = k pi (3 - sqrt 5);
+* Mn9-like centred cube (Sec. III.C; the published couplings are not
+  available here, so the values below are synthetic): a spin-5/2 at the
+  centre, eight spin-2 at the vertices of a cube of edge a (top square
+  z = +a/2, bottom z = -a/2, vertex k at azimuth 45 + 90 k degrees); J_c
+  centre-vertex, J_s nearest neighbours within the top and within the
+  bottom square, J_e the vertical edges; each vertex has an easy axis
+  (d < 0) tilted 30 degrees from z, at azimuth +10 degrees (top) or -10
+  degrees (bottom) from the x axis; powder average over the 10 directions
+  through the vertices of a dodecahedron, one of each antipodal pair
+  (B and -B give the same thermodynamics).
 """
 from __future__ import annotations
 
@@ -173,10 +183,58 @@ def chain_batch():
     return out
 
 
+def dodecahedron_directions():
+    """10 unit vectors: one vertex of each antipodal pair of a regular
+    dodecahedron, (1,1,1)-type and the cyclic (0, 1/phi, phi) family."""
+    ph = (1 + np.sqrt(5.0)) / 2
+    v = [(1, 1, 1), (1, 1, -1), (1, -1, 1), (1, -1, -1),
+         (0, 1 / ph, ph), (0, 1 / ph, -ph), (1 / ph, ph, 0), (1 / ph, -ph, 0), (ph, 0, 1 / ph), (ph, 0, -1 / ph)]
+    v = np.asarray(v, dtype=np.float64)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def mn9(Bdir=(0, 0, 1), B=1.0, vertices=8, a=3.6, Jc=-1.2, Js=0.4, Je=0.25, D=-1.5):
+    """Mn9-like centred cube: site 0 spin 5/2 at the centre, sites 1..8 spin 2
+    at the cube vertices (1-4 top, 5-8 bottom); `vertices` < 8 keeps the first
+    ones (a smaller test system).  d = 6 * 5^vertices (2,343,750 for 8)."""
+    n = 1 + vertices
+    pos = np.zeros((n, 3))
+    axes = np.zeros((n, 3))
+    d_ion = np.zeros(n)
+    for k in range(vertices):
+        top = k < 4
+        az = np.deg2rad(45 + 90 * (k % 4))
+        pos[1 + k] = (a / np.sqrt(2) * np.cos(az), a / np.sqrt(2) * np.sin(az), a / 2 if top else -a / 2)
+        phi = np.deg2rad(10 if top else -10)
+        th = np.deg2rad(30)
+        axes[1 + k] = (np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th))
+        d_ion[1 + k] = D
+    axes[0] = (0, 0, 1)
+    J = np.zeros((n, n))
+    for k in range(vertices):
+        J[0, 1 + k] = Jc
+    for k in range(vertices):
+        for l in range(k + 1, vertices):
+            same = (k < 4) == (l < 4)
+            if same and (l - k) % 4 in (1, 3):     # neighbours within a square
+                J[1 + k, 1 + l] = Js
+            elif not same and l - k == 4:          # vertical edge
+                J[1 + k, 1 + l] = Je
+    bd = np.asarray(Bdir, dtype=np.float64)
+    bd = bd / np.linalg.norm(bd)
+    return _system(f"mn9_{vertices}", [5] + [4] * vertices, J, pos, B * bd, g=2.0, d_ion=d_ion, e_axes=axes)
+
+
+def mn9_powder():
+    """The Mn9-like system at 1 T along each of the 10 dodecahedron directions."""
+    return [mn9(Bdir=u) for u in dodecahedron_directions()]
+
+
 WORKLOADS = {
     "ring6_s1": dict(system=ring6_s1, R=10, M=80, dtype="c128", seed=0),
     "lattice4x4": dict(system=lattice4x4, R=50, M=150, dtype="c128", seed=1),
     "lattice4x5": dict(system=lattice4x5, R=64, M=200, dtype="c64", seed=2),
     "chains_s1_x24": dict(system=chain_batch, R=16, M=120, dtype="c64", seed=3),
     "ladder2x13": dict(system=ladder2x13, R=4, M=300, dtype="c64", seed=4),
+    "mn9_powder": dict(system=mn9_powder, R=8, M=40, dtype="c64", seed=5),
 }

@@ -64,7 +64,8 @@ typedef enum {
 typedef enum {
   FTLM_START_RANDOM = 0, /* Gaussian random vectors, Eq. (2) */
   FTLM_START_BASIS = 1,  /* basis vectors |basis_offset + k>, k = 0..R-1 */
-  FTLM_START_USER = 2    /* caller's device block [dim][R] of the run's dtype */
+  FTLM_START_USER = 2,   /* caller's device block [dim][R] of the run's dtype */
+  FTLM_START_PAIRS = 3   /* pairs of time-reversed random vectors (ftlm_start_pairs) */
 } ftlm_start_mode;
 
 /* Physical constants used by Eq. (3); NULL selects the defaults
@@ -146,6 +147,31 @@ ftlm_status ftlm_apply_sdir(const ftlm_system* sys, const double* u, const void*
  * any nvec, offset or dtype (up to the final rounding).
  */
 ftlm_status ftlm_start_block(const ftlm_system* sys, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                             ftlm_dtype dtype, void* stream);
+
+/*
+ * ftlm_time_reverse -- y = Theta x for every column of a block, with Theta =
+ * exp(-i pi S^y) K the time-reversal operator (Sec. II.B: the symmetry behind
+ * the pairs of mutually time-reversed random vectors): on one site
+ * exp(-i pi s^y)|s,m> = (-1)^(s-m)|s,-m>, K conjugates the coefficients, so
+ *   y[nu][k] = (-1)^(sum_i a_i(nu)) conj(x[dim - 1 - nu][k])
+ * (the digit map a_i -> 2 s_i - a_i reverses the basis index).
+ *  x, y   device blocks [dim][nvec] of dtype, 16-byte aligned, not
+ *         overlapping (FTLM_ERR_INVALID_ARG otherwise).
+ * Asynchronous on stream (NULL = the default stream).
+ */
+ftlm_status ftlm_time_reverse(const ftlm_system* sys, const void* x, void* y, int nvec, ftlm_dtype dtype,
+                              void* stream);
+
+/*
+ * ftlm_start_pairs -- start vectors in pairs of mutually time-reversed random
+ * vectors (Sec. II.B; tau = 1 in Sec. III): global vector number
+ * v = vec_offset + k is random vector v / 2 of ftlm_start_block (same seed)
+ * when v is even, and Theta applied to it when v is odd, each normalised to 1.
+ * Arguments, layout and stream behaviour as ftlm_start_block; ftlm_run's
+ * FTLM_START_PAIRS generates the same vectors.
+ */
+ftlm_status ftlm_start_pairs(const ftlm_system* sys, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
                              ftlm_dtype dtype, void* stream);
 
 /*

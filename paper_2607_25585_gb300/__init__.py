@@ -21,7 +21,7 @@ from . import _build
 _LIB_PATH = _build.LIB
 
 C128, C64 = 0, 1
-START_RANDOM, START_BASIS, START_USER = 0, 1, 2
+START_RANDOM, START_BASIS, START_USER, START_PAIRS = 0, 1, 2, 3
 _DTYPES = {"c128": C128, "complex128": C128, C128: C128, "c64": C64, "complex64": C64, C64: C64}
 _STATUS = {0: "FTLM_OK", 1: "FTLM_ERR_INVALID_ARG", 2: "FTLM_ERR_OUT_OF_MEMORY", 3: "FTLM_ERR_CUDA",
            4: "FTLM_ERR_TIMEOUT", 5: "FTLM_ERR_UNSUPPORTED", 6: "FTLM_ERR_NUMERICAL"}
@@ -65,7 +65,8 @@ class Result(ctypes.Structure):
 # every symbol include/ftlm.h declares
 EXPORTS = ["ftlm_system_create", "ftlm_system_destroy", "ftlm_system_dim", "ftlm_system_table_bytes",
            "ftlm_apply_h", "ftlm_apply_sdir",
-           "ftlm_start_block", "ftlm_start_block_noalloc", "ftlm_run", "ftlm_run_batch", "ftlm_sums",
+           "ftlm_start_block", "ftlm_start_block_noalloc", "ftlm_start_pairs", "ftlm_time_reverse",
+           "ftlm_run", "ftlm_run_batch", "ftlm_sums",
            "ftlm_tune_shape", "ftlm_last_error", "ftlm_version"]
 
 _lib = None
@@ -96,6 +97,8 @@ def lib():
         L.ftlm_apply_sdir.argtypes = [vp, pd, vp, vp, i, i, vp]
         L.ftlm_start_block.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp, i, i, vp]
         L.ftlm_start_block_noalloc.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp, i, i, vp]
+        L.ftlm_start_pairs.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp, i, i, vp]
+        L.ftlm_time_reverse.argtypes = [vp, vp, vp, i, i, vp]
         L.ftlm_run.argtypes = [vp, P(RunParams), P(Result)]
         L.ftlm_run_batch.argtypes = [i, P(vp), P(RunParams), P(Result)]
         L.ftlm_sums.argtypes = [i, i, P(i), pd, pd, pd, d, d, pd, i, P(Result)]
@@ -219,6 +222,17 @@ def start_block(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dty
                                   _stream(stream, out)))
 
 
+def start_pairs(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dtype="c64", stream=None):
+    """Normalised pairs of time-reversed random vectors (``ftlm_start_pairs``)."""
+    _check(lib().ftlm_start_pairs(sys.handle, int(seed), int(vec_offset), _ptr(out), int(nvec), _DTYPES[dtype],
+                                  _stream(stream, out)))
+
+
+def time_reverse(sys: System, x, y, nvec: int, dtype="c64", stream=None):
+    """y = Theta x, Theta = exp(-i pi S^y) K (``ftlm_time_reverse``)."""
+    _check(lib().ftlm_time_reverse(sys.handle, _ptr(x), _ptr(y), int(nvec), _DTYPES[dtype], _stream(stream, x)))
+
+
 def start_block_noalloc(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dtype="c64", stream=None):
     """``ftlm_start_block`` without any device allocation, for callers that
     may not allocate (``ftlm_start_block_noalloc``): its scratch is a static
@@ -233,7 +247,8 @@ def _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, o
     T = _f64(T)
     od = _f64(obs_dir)
     keep += [T, od]
-    mode = {"random": START_RANDOM, "basis": START_BASIS, "user": START_USER}[start] if isinstance(start, str) \
+    mode = {"random": START_RANDOM, "basis": START_BASIS, "user": START_USER, "pairs": START_PAIRS}[start] \
+        if isinstance(start, str) \
         else int(start)
     return RunParams(int(R), int(M), int(seed), int(vec_offset), _DTYPES[dtype], mode, int(basis_offset),
                      _ptr(user_start), _pd(T), len(T), _pd(od), float(breakdown_tol), int(autotune),
@@ -273,10 +288,11 @@ def run(sys: System, R: int, M: int, T, seed: int = 0, vec_offset: int = 0, dtyp
 
 
 def run_batch(systems, R: int, M: int, T, seed: int = 0, vec_offset: int = 0, dtype="c64", obs_dir=None,
-              breakdown_tol: float = 0.0, autotune=False, time_kernels=False, stream=None) -> list:
-    """FTLM for several systems in one graph (``ftlm_run_batch``)."""
+              breakdown_tol: float = 0.0, autotune=False, time_kernels=False, stream=None, start="random") -> list:
+    """FTLM for several systems in one graph (``ftlm_run_batch``); start is
+    "random", "pairs" or "basis"."""
     keep = []
-    p = _params(R, M, T, seed, vec_offset, dtype, "random", 0, None, obs_dir, breakdown_tol, autotune, time_kernels,
+    p = _params(R, M, T, seed, vec_offset, dtype, start, 0, None, obs_dir, breakdown_tol, autotune, time_kernels,
                 stream, keep)
     n = len(systems)
     rs, outs = [], []

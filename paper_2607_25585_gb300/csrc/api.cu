@@ -525,7 +525,7 @@ ftlm_status validate_params(const ftlm_run_params* p, const std::vector<ftlm_sys
   if (!p->T || p->nT < 1) return fail(FTLM_ERR_INVALID_ARG, "temperature grid missing");
   for (int t = 0; t < p->nT; ++t)
     if (!(p->T[t] > 0.0) || !std::isfinite(p->T[t])) return fail(FTLM_ERR_INVALID_ARG, "temperatures must be > 0");
-  if (p->start < 0 || p->start > 2) return fail(FTLM_ERR_INVALID_ARG, "unknown start mode");
+  if (p->start < 0 || p->start > 3) return fail(FTLM_ERR_INVALID_ARG, "unknown start mode");
   if (p->start == FTLM_START_USER && !p->user_start) return fail(FTLM_ERR_INVALID_ARG, "user_start is NULL");
   if (p->start == FTLM_START_USER && (reinterpret_cast<uintptr_t>(p->user_start) & 15))
     return fail(FTLM_ERR_INVALID_ARG, "user_start must be 16-byte aligned");
@@ -575,6 +575,8 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
     const long long dim = (long long)sys[k]->hs.dim;
     if (p->start == FTLM_START_RANDOM)
       CKI(launch_start_random(&h, nullptr, R, p->seed, p->vec_offset, sys[k]->A.p, c64, st, vmaj));
+    else if (p->start == FTLM_START_PAIRS)
+      CKI(launch_start_pairs(&h, R, p->seed, p->vec_offset, sys[k]->A.p, c64, st, vmaj));
     else if (p->start == FTLM_START_BASIS)
       CKI(launch_start_basis(dim, R, p->basis_offset, sys[k]->A.p, c64, st, vmaj));
     else if (vmaj)
@@ -1105,8 +1107,13 @@ ftlm_status ftlm_apply_sdir(const ftlm_system* s, const double* u, const void* x
   return rows_entry(s, kModeApplyS, u, x, y, nvec, dtype, stream);
 }
 
-ftlm_status ftlm_start_block(const ftlm_system* cs, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
-                             ftlm_dtype dtype, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Normalised start block: plain random vectors, or pairs of time-reversed ones.
+ftlm_status start_block_impl(const ftlm_system* cs, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                             ftlm_dtype dtype, void* stream, bool pairs) {
   ftlm_status v = check_block_args(cs, out, out, nvec, dtype);
   if (v != FTLM_OK) return v;
   const int c64 = dtype == FTLM_C64;
@@ -1126,7 +1133,8 @@ ftlm_status ftlm_start_block(const ftlm_system* cs, uint64_t seed, uint64_t vec_
   }
   if (s->esc.bytes < scalar_bytes(nvec, 1)) CK(s->esc.ensure(scalar_bytes(nvec, 1)));
   InstDesc h = base_desc(s, c64);
-  CKI(launch_start_random(&h, nullptr, nvec, seed, vec_offset, out, c64, st));
+  if (pairs) CKI(launch_start_pairs(&h, nvec, seed, vec_offset, out, c64, st, 0));
+  else CKI(launch_start_random(&h, nullptr, nvec, seed, vec_offset, out, c64, st));
   LaunchArgs a = pl.base;
   a.inline_one = 1;
   a.one = h;
@@ -1140,6 +1148,33 @@ ftlm_status ftlm_start_block(const ftlm_system* cs, uint64_t seed, uint64_t vec_
   CKI(launch_rows(a, c64, pl.grid, pl.sh.threads, pl.smem, st));
   a.mode = kModeScale;
   CKI(launch_rows(a, c64, pl.grid, pl.sh.threads, pl.smem, st));
+  return FTLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ftlm_status ftlm_start_block(const ftlm_system* cs, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                             ftlm_dtype dtype, void* stream) {
+  return start_block_impl(cs, seed, vec_offset, out, nvec, dtype, stream, false);
+}
+
+ftlm_status ftlm_start_pairs(const ftlm_system* cs, uint64_t seed, uint64_t vec_offset, void* out, int nvec,
+                             ftlm_dtype dtype, void* stream) {
+  return start_block_impl(cs, seed, vec_offset, out, nvec, dtype, stream, true);
+}
+
+ftlm_status ftlm_time_reverse(const ftlm_system* cs, const void* x, void* y, int nvec, ftlm_dtype dtype,
+                              void* stream) {
+  ftlm_status v = check_block_args(cs, x, y, nvec, dtype);
+  if (v != FTLM_OK) return v;
+  const int c64 = dtype == FTLM_C64;
+  const size_t bytes = (size_t)cs->hs.dim * nvec * (c64 ? 8 : 16);
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+  if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
+  InstDesc h = base_desc(cs, c64);
+  CKI(launch_time_reverse(&h, x, y, nvec, c64, pick_stream(cs, stream)));
   return FTLM_OK;
 }
 

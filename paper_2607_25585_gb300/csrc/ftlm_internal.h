@@ -178,6 +178,10 @@ int launch_start_random(const InstDesc* inst_host, const InstDesc* inst_dev, int
 int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream,
                        int vector_major = 0);
 int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int c64, void* stream);
+// pairs of time-reversed random vectors (unnormalised) and y = Theta x on [d][R]
+int launch_start_pairs(const InstDesc* h, int R, uint64_t seed, uint64_t vec_offset, void* out, int c64,
+                       void* stream, int vector_major);
+int launch_time_reverse(const InstDesc* h, const void* x, void* y, int R, int c64, void* stream);
 int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
 size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads);
 int prepare_rows_kernels(size_t smem);

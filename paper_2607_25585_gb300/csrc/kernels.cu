@@ -478,6 +478,87 @@ __global__ void start_basis_kernel(long long dim, int R, unsigned long long basi
   }
 }
 
+// Parity of the digit sum sum_i a_i(nu) (a_i = m_i + s_i): the sign of the
+// time-reversed basis state, (-1)^(sum_i (s_i - m_i)) at the image (Sec. II.B).
+__device__ __forceinline__ int digit_parity(long long nu, int n, const int* q, int all_half) {
+  if (all_half) return __popcll((unsigned long long)nu) & 1;
+  int sum = 0;
+  for (int i = 0; i < n; ++i) {
+    const int qi = __ldg(q + i);
+    sum += (int)(nu % qi);
+    nu /= qi;
+  }
+  return sum & 1;
+}
+
+// Pairs of mutually time-reversed random vectors (Sec. II.B, tau = 1 in
+// Sec. III): global vector v = vec_offset + k is random vector v / 2 of the
+// Philox stream when v is even and its time reverse when v is odd,
+//   (Theta r)[nu] = (-1)^(sum_i a_i(nu)) conj(r[d - 1 - nu]),
+// since Theta = exp(-i pi S^y) K maps every digit a_i to 2 s_i - a_i, i.e.
+// the index nu to d - 1 - nu.  Unnormalised, like start_random_kernel.
+template <typename real, bool VMAJ>
+__global__ void start_pairs_kernel(long long dim, int R, unsigned long long seed, unsigned long long vec_offset,
+                                   int n, const int* q, int all_half, real* out) {
+  const long long total = dim * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long nu = VMAJ ? e % dim : e / R;
+    const unsigned long long v = vec_offset + (unsigned long long)(VMAJ ? e / dim : e - nu * R);
+    const bool rev = (v & 1ull) != 0;
+    const long long src = rev ? dim - 1 - nu : nu;
+    const unsigned long long rg = v >> 1;
+    unsigned c[4] = {(unsigned)src, (unsigned)((unsigned long long)src >> 32), (unsigned)rg, (unsigned)(rg >> 32)};
+    philox4x32_10(c, (unsigned)seed, (unsigned)(seed >> 32));
+    const double u1 = unit53(c[0], c[1]);
+    const double u2 = unit53(c[2], c[3]);
+    const double rho = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    double re = rho * cs, im = rho * sn;
+    if (rev) {
+      im = -im;
+      if (digit_parity(nu, n, q, all_half)) {
+        re = -re;
+        im = -im;
+      }
+    }
+    out[2 * e] = (real)re;
+    out[2 * e + 1] = (real)im;
+  }
+}
+
+// y = Theta x on a row-major [d][R] block: y[nu][k] = (-1)^(sum a_i(nu)) conj(x[d-1-nu][k]).
+// V consecutive vectors of a row per thread (16-byte accesses for complex64
+// with even R), two items per loop trip.
+template <typename real, int V>
+__global__ void time_reverse_kernel(long long dim, int R, int n, const int* q, int all_half, const real* x,
+                                    real* y) {
+  const long long items = dim * R / V;
+  const int C = R / V;  // items per row
+  auto one = [&](long long it) {
+    const long long nu = it / C;
+    const long long idx = it * V;               // complex index of the first value
+    const long long src = (dim - 1 - nu) * R + (idx - nu * R);
+    real re[V], im[V];
+    VecIO<real, V>::ldg(x, src, re, im);
+    const real sg = digit_parity(nu, n, q, all_half) ? (real)-1 : (real)1;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      re[v] *= sg;
+      im[v] *= -sg;
+    }
+    VecIO<real, V>::st(y, idx, re, im);
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; it + stride < items; it += 2 * stride) {
+    one(it);
+    one(it + stride);
+  }
+  if (it < items) one(it);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -584,6 +665,38 @@ int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, i
     if (vector_major) start_basis_kernel<double, true><<<grid, 256, 0, st>>>(dim, R, basis_offset, (double*)out);
     else start_basis_kernel<double, false><<<grid, 256, 0, st>>>(dim, R, basis_offset, (double*)out);
   }
+  return (int)cudaGetLastError();
+}
+
+int launch_start_pairs(const InstDesc* h, int R, uint64_t seed, uint64_t vec_offset, void* out, int c64,
+                       void* stream, int vector_major) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long dim = h->dim;
+  const int grid = elementwise_grid(dim * R);
+  if (c64) {
+    if (vector_major)
+      start_pairs_kernel<float, true><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, h->n, h->q, h->all_half, (float*)out);
+    else
+      start_pairs_kernel<float, false><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, h->n, h->q, h->all_half, (float*)out);
+  } else {
+    if (vector_major)
+      start_pairs_kernel<double, true><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, h->n, h->q, h->all_half, (double*)out);
+    else
+      start_pairs_kernel<double, false><<<grid, 256, 0, st>>>(dim, R, seed, vec_offset, h->n, h->q, h->all_half, (double*)out);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_time_reverse(const InstDesc* h, const void* x, void* y, int R, int c64, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long dim = h->dim;
+  const int grid = elementwise_grid(dim * R);
+  if (c64 && R % 2 == 0)
+    time_reverse_kernel<float, 2><<<grid, 256, 0, st>>>(dim, R, h->n, h->q, h->all_half, (const float*)x, (float*)y);
+  else if (c64)
+    time_reverse_kernel<float, 1><<<grid, 256, 0, st>>>(dim, R, h->n, h->q, h->all_half, (const float*)x, (float*)y);
+  else
+    time_reverse_kernel<double, 1><<<grid, 256, 0, st>>>(dim, R, h->n, h->q, h->all_half, (const double*)x, (double*)y);
   return (int)cudaGetLastError();
 }
 

@@ -165,3 +165,17 @@ def test_oracle_total_spin(rng):
     O = dense.total_spin_along(s, u)
     X = rng.normal(size=(s.dim, 2)) + 1j * rng.normal(size=(s.dim, 2))
     assert np.allclose(oracle.apply_sdir(s, u, X), O @ X, atol=1e-13)
+
+
+def test_dodecahedron_directions():
+    """The powder-average directions with their antipodes are the 20 vertices
+    of a regular dodecahedron: unit vectors, and the shortest distance between
+    two of them occurs exactly 30 times (the 30 edges)."""
+    import ftlm_workloads as W
+    u = W.dodecahedron_directions()
+    v = np.concatenate([u, -u])
+    assert np.allclose(np.linalg.norm(v, axis=1), 1.0)
+    dist = np.linalg.norm(v[:, None, :] - v[None, :, :], axis=2)
+    iu = np.triu_indices(20, 1)
+    dd = dist[iu]
+    assert np.sum(np.isclose(dd, dd.min())) == 30 and dd.min() > 0.5
