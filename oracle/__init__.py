@@ -76,6 +76,9 @@ def _load():
         _lib.oracle_apply_h.argtypes = [P(_CSystem), pd, pd, i64]
         _lib.oracle_apply_sdir.argtypes = [P(_CSystem), pd, pd, pd, i64]
         _lib.oracle_time_reverse.argtypes = [P(_CSystem), pd, pd, i64]
+        _lib.oracle_sftlm_sums.argtypes = [i32, i32, P(i32), pd, pd, pd, d, pd, i32, pd, pd]
+        _lib.oracle_sftlm.argtypes = [P(_CSystem), i32, i32, u64, u64, i32, i64, pd, i32, d, pd, pd, i32,
+                                      pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, P(i32)]
         _lib.oracle_h_column.restype = i64
         _lib.oracle_h_column.argtypes = [P(_CSystem), i64, P(i64), pd, i64]
         _lib.oracle_philox4x32_10.argtypes = [P(ctypes.c_uint32)] * 3
@@ -331,6 +334,48 @@ def ftlm(sys: System, R: int, M: int, T=None, seed: int = 0, vec_offset: int = 0
     assert rc == 0, "oracle_ftlm failed"
     out.update(E0=float(E0[0]), alpha=a, beta=b, p=p, M_eff=me, T=T)
     return out
+
+
+def sftlm(sys: System, R: int, M: int, T=None, seed: int = 0, vec_offset: int = 0, start: str = "random",
+          basis_offset: int = 0, user_start=None, reorth: bool = False, tol: float = 1e-12, direction=None):
+    """FTLM plus symmetric FTLM (Eqs. E-2-G, E-2-H) for O = dir.S: the dict of
+    ``ftlm`` plus M_B_sym, M_B_sym_imag and O[r, i, j] = <v_i|O|v_j>."""
+    lib = _load()
+    T = default_temperatures() if T is None else np.ascontiguousarray(T, dtype=np.float64)
+    nT = len(T)
+    mode = {"random": 0, "basis": 1, "user": 2, "pairs": 3}[start]
+    us = _cx(user_start).reshape(sys.dim, R) if mode == 2 else None
+    keys = ("lnZ", "E", "C", "M_B", "M_B_imag", "M_B_sym", "M_B_sym_imag")
+    out = {k: np.empty(nT) for k in keys}
+    E0 = np.zeros(1)
+    a = np.zeros((R, M))
+    b = np.zeros((R, M))
+    O = np.zeros((R, M, M), dtype=np.complex128)
+    me = np.zeros(R, dtype=np.int32)
+    u = None if direction is None else np.ascontiguousarray(direction, dtype=np.float64)
+    cs = sys.c()
+    rc = lib.oracle_sftlm(ctypes.byref(cs), R, M, seed, vec_offset, mode, basis_offset,
+                          _pd(us.view(np.float64)) if us is not None else None, int(reorth), tol, _pd(u), _pd(T), nT,
+                          *[_pd(out[k]) for k in keys], _pd(E0), _pd(a), _pd(b), _pd(O.view(np.float64)),
+                          me.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    assert rc == 0, "oracle_sftlm failed"
+    out.update(E0=float(E0[0]), alpha=a, beta=b, O=O, M_eff=me, T=T)
+    return out
+
+
+def sftlm_sums(alpha, beta, O, M_eff, g, T):
+    """M_B_sym, M_B_sym_imag of Eqs. (E-2-G), (E-2-H) from per-run data."""
+    lib = _load()
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    R, M = a.shape
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    Oc = _cx(O)
+    me = np.ascontiguousarray(M_eff, dtype=np.int32)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    mb, mbi = np.empty(len(T)), np.empty(len(T))
+    assert lib.oracle_sftlm_sums(R, M, me.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _pd(a), _pd(b),
+                                 _pd(Oc.view(np.float64)), float(g), _pd(T), len(T), _pd(mb), _pd(mbi)) == 0
+    return mb, mbi
 
 
 def num_threads() -> int:

@@ -15,6 +15,9 @@
 //     re-orthogonalisation (Sec. II.C);
 //   * the FTLM estimators Eq. (4) (observable ratio, same r in numerator and
 //     denominator) and Eq. (5) (partition function, Gamma = 1: no symmetry);
+//   * symmetric FTLM (sFTLM), Eqs. (E-2-G) and (E-2-H): the observable
+//     between the two halves of e^{-beta H}, with <m|O|n> from the matrix of
+//     O in the Lanczos basis;
 //   * pairs of mutually time-reversed random vectors (Sec. II.B: the
 //     time-reversal symmetry used for the FTLM approximation, tau = 1 in the
 //     figures of Sec. III), Theta = exp(-i pi S^y) K with K the complex
@@ -345,13 +348,16 @@ cplx dot(const std::vector<cplx>& a, const std::vector<cplx>& b) {  // <a|b>
 
 // v0 must be normalised.  alpha[M], beta[M] (beta[j] = norm after step j, the
 // off-diagonal T[j][j+1]), p[M] = <v_j | u>, u = (dir.S) v0.
+// keep: if given, receives the Lanczos vectors v_0 .. v_{M_eff-1}.
 int lanczos(const Model& M, const std::vector<PairLadder>& PL, const std::vector<cplx>& v0, int maxM,
-            int reorth, double tol, const double* dir, double* alpha, double* beta, cplx* p) {
+            int reorth, double tol, const double* dir, double* alpha, double* beta, cplx* p,
+            std::vector<std::vector<cplx>>* keep = nullptr) {
   const int64_t d = M.dim;
   std::vector<cplx> u(d), w(d), vprev(d, 0.0), v = v0;
   apply_sdir(M, dir, v0.data(), u.data(), 1);
   std::vector<std::vector<cplx>> basis;
   if (reorth) basis.push_back(v);
+  if (keep) keep->assign(1, v);
   double bj = 0.0, scale = 0.0;
   int meff = maxM;
   for (int j = 0; j < maxM; ++j) {
@@ -380,8 +386,10 @@ int lanczos(const Model& M, const std::vector<PairLadder>& PL, const std::vector
     vprev = v;
     for (int64_t i = 0; i < d; ++i) v[i] = w[i] / nb;
     if (reorth) basis.push_back(v);
+    if (keep) keep->push_back(v);
     bj = nb;
   }
+  if (keep) keep->resize(meff);
   return meff;
 }
 
@@ -452,8 +460,42 @@ void time_reverse(const Model& M, const cplx* x, cplx* y, int64_t nvec) {
   }
 }
 
-}  // namespace
+// Start vector number r of a run of R (Eq. 2 and the start modes): 0 = Philox
+// random vector vec_offset + r, 1 = basis vector |basis_offset + r>, 2 = column
+// r of the user block [d][R], 3 = time-reversed pairs (vector v = vec_offset + r
+// is random vector v / 2, time-reversed when v is odd).  Normalised to 1.
+bool start_vector(const Model& M, int r, int R, uint64_t seed, uint64_t vec_offset, int start_mode,
+                  int64_t basis_offset, const double* user_start, std::vector<cplx>& v0) {
+  v0.assign(M.dim, 0.0);
+  auto normalise = [](std::vector<cplx>& v) {
+    double nrm = 0.0;
+    for (const auto& z : v) nrm += std::norm(z);
+    nrm = std::sqrt(nrm);
+    for (auto& z : v) z /= nrm;
+  };
+  if (start_mode == 0) {
+    for (int64_t nu = 0; nu < M.dim; ++nu) v0[nu] = gaussian_component(seed, vec_offset + (uint64_t)r, (uint64_t)nu);
+    normalise(v0);
+  } else if (start_mode == 3) {
+    const uint64_t v = vec_offset + (uint64_t)r;
+    std::vector<cplx> rk(M.dim);
+    for (int64_t nu = 0; nu < M.dim; ++nu) rk[nu] = gaussian_component(seed, v / 2, (uint64_t)nu);
+    normalise(rk);
+    if (v % 2) time_reverse(M, rk.data(), v0.data(), 1);
+    else v0 = rk;
+  } else if (start_mode == 1) {
+    const int64_t b = basis_offset + r;
+    if (b < 0 || b >= M.dim) return false;
+    v0[b] = 1.0;
+  } else {
+    const cplx* us = reinterpret_cast<const cplx*>(user_start);
+    for (int64_t nu = 0; nu < M.dim; ++nu) v0[nu] = us[nu * R + r];
+    normalise(v0);
+  }
+  return true;
+}
 
+}  // namespace
 
 extern "C" {
 
@@ -639,43 +681,10 @@ int oracle_ftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t
 #pragma omp parallel for schedule(dynamic, 1)
   for (int r = 0; r < R; ++r) {
     std::vector<cplx> v0(M.dim, 0.0);
-    if (start_mode == 0) {
-      double nrm = 0.0;
-      for (int64_t nu = 0; nu < M.dim; ++nu) {
-        v0[nu] = gaussian_component(seed, vec_offset + (uint64_t)r, (uint64_t)nu);
-        nrm += std::norm(v0[nu]);
-      }
-      nrm = std::sqrt(nrm);
-      for (auto& z : v0) z /= nrm;
-    } else if (start_mode == 3) {  // time-reversed pairs: vector 2k = r_k, 2k + 1 = Theta r_k
-      const uint64_t v = vec_offset + (uint64_t)r;
-      std::vector<cplx> rk(M.dim);
-      double nrm = 0.0;
-      for (int64_t nu = 0; nu < M.dim; ++nu) {
-        rk[nu] = gaussian_component(seed, v / 2, (uint64_t)nu);
-        nrm += std::norm(rk[nu]);
-      }
-      nrm = std::sqrt(nrm);
-      for (auto& z : rk) z /= nrm;
-      if (v % 2) time_reverse(M, rk.data(), v0.data(), 1);
-      else v0 = rk;
-    } else if (start_mode == 1) {
-      int64_t b = basis_offset + r;
-      if (b < 0 || b >= M.dim) {
+    if (!start_vector(M, r, R, seed, vec_offset, start_mode, basis_offset, user_start, v0)) {
 #pragma omp atomic write
-        fail = 1;
-        continue;
-      }
-      v0[b] = 1.0;
-    } else {
-      const cplx* us = reinterpret_cast<const cplx*>(user_start);
-      double nrm = 0.0;
-      for (int64_t nu = 0; nu < M.dim; ++nu) {
-        v0[nu] = us[nu * R + r];
-        nrm += std::norm(v0[nu]);
-      }
-      nrm = std::sqrt(nrm);
-      for (auto& z : v0) z /= nrm;
+      fail = 1;
+      continue;
     }
     meff[r] = lanczos(M, PL, v0, maxM, reorth, tol, u, &alpha[(size_t)r * maxM], &beta[(size_t)r * maxM],
                       &p[(size_t)r * maxM]);
@@ -686,6 +695,101 @@ int oracle_ftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t
   if (alpha_out) std::memcpy(alpha_out, alpha.data(), sizeof(double) * alpha.size());
   if (beta_out) std::memcpy(beta_out, beta.data(), sizeof(double) * beta.size());
   if (p_out) std::memcpy(p_out, p.data(), sizeof(cplx) * p.size());
+  if (meff_out) std::memcpy(meff_out, meff.data(), sizeof(int) * meff.size());
+  return rc;
+}
+
+// Symmetric FTLM for O = dir.S, Eqs. (E-2-G) and (E-2-H): per run r
+//   <r|e^{-beta H/2} O e^{-beta H/2}|r> ~ sum_{m,n} e^{-beta (eps_m + eps_n)/2}
+//        <r|m> <m|O|n> <n|r>,   <m|O|n> = sum_{i,j} U_im O_ij U_jn,
+// O_ij = <v_i|O|v_j> in the Lanczos basis, <r|n> = U_0n; the denominator
+// <r|e^{-beta H}|r> = sum_n e^{-beta eps_n} |U_0n|^2.  Both shifted by E0 (the
+// lowest Ritz value over all runs).  Omat: [R][M][M] complex, Omat[r][i][j] =
+// O_ij.  Outputs MB_sym = -g Re(num / den), MB_sym_imag = -g Im(num / den).
+int oracle_sftlm_sums(int R, int maxM, const int* M_eff, const double* alpha, const double* beta,
+                      const double* Omat, double g, const double* T, int nT, double* MB_sym, double* MB_sym_imag) {
+  if (R <= 0 || maxM <= 0 || nT <= 0) return -1;
+  std::vector<std::vector<double>> ev(R), U(R);
+  std::vector<std::vector<cplx>> Ot(R);  // <m|O|n>
+  double E0 = INFINITY;
+  for (int r = 0; r < R; ++r) {
+    const int m = M_eff[r];
+    if (m <= 0 || m > maxM) return -1;
+    ev[r].resize(m);
+    U[r].resize((size_t)m * m);
+    jacobi_tridiag(m, alpha + (size_t)r * maxM, beta + (size_t)r * maxM, ev[r].data(), U[r].data());
+    for (int nn = 0; nn < m; ++nn) E0 = std::min(E0, ev[r][nn]);
+    const cplx* O = reinterpret_cast<const cplx*>(Omat) + (size_t)r * maxM * maxM;
+    Ot[r].assign((size_t)m * m, 0.0);
+    for (int mm = 0; mm < m; ++mm)
+      for (int nn = 0; nn < m; ++nn) {
+        cplx acc = 0.0;
+        for (int i = 0; i < m; ++i)
+          for (int j = 0; j < m; ++j) acc += U[r][(size_t)i * m + mm] * O[(size_t)i * maxM + j] * U[r][(size_t)j * m + nn];
+        Ot[r][(size_t)mm * m + nn] = acc;
+      }
+  }
+  for (int t = 0; t < nT; ++t) {
+    const double b = 1.0 / T[t];
+    double den = 0.0;
+    cplx num = 0.0;
+    for (int r = 0; r < R; ++r) {
+      const int m = M_eff[r];
+      for (int nn = 0; nn < m; ++nn) den += std::exp(-b * (ev[r][nn] - E0)) * U[r][nn] * U[r][nn];
+      for (int mm = 0; mm < m; ++mm)
+        for (int nn = 0; nn < m; ++nn)
+          num += std::exp(-0.5 * b * (ev[r][mm] + ev[r][nn] - 2.0 * E0)) * U[r][mm] * Ot[r][(size_t)mm * m + nn] *
+                 U[r][nn];
+    }
+    MB_sym[t] = -g * std::real(num) / den;
+    MB_sym_imag[t] = -g * std::imag(num) / den;
+  }
+  return 0;
+}
+
+// Lanczos runs that also return O_ij = <v_i|dir.S|v_j> for each run
+// (Omat [R][M][M] complex, zero outside M_eff), with the start modes of
+// oracle_ftlm; then the FTLM outputs of oracle_ftlm_sums and the sFTLM
+// M_B of oracle_sftlm_sums.
+int oracle_sftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t vec_offset, int start_mode,
+                 int64_t basis_offset, const double* user_start, int reorth, double tol, const double* dir,
+                 const double* T, int nT, double* lnZ, double* E, double* C, double* MB, double* MB_imag,
+                 double* MB_sym, double* MB_sym_imag, double* E0, double* alpha_out, double* beta_out,
+                 double* Omat_out, int* meff_out) {
+  Model M;
+  if (!build_model(s, M) || R <= 0 || maxM <= 0 || nT <= 0) return -1;
+  auto PL = all_pair_ladders(M);
+  const double* u = dir ? dir : M.Bdir;
+  std::vector<double> alpha((size_t)R * maxM, 0.0), beta((size_t)R * maxM, 0.0);
+  std::vector<cplx> p((size_t)R * maxM, 0.0), O((size_t)R * maxM * maxM, 0.0);
+  std::vector<int> meff(R, 0);
+  int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    std::vector<cplx> v0;
+    if (!start_vector(M, r, R, seed, vec_offset, start_mode, basis_offset, user_start, v0)) {
+#pragma omp atomic write
+      fail = 1;
+      continue;
+    }
+    std::vector<std::vector<cplx>> V;
+    meff[r] = lanczos(M, PL, v0, maxM, reorth, tol, u, &alpha[(size_t)r * maxM], &beta[(size_t)r * maxM],
+                      &p[(size_t)r * maxM], &V);
+    std::vector<cplx> w(M.dim);
+    for (int j = 0; j < meff[r]; ++j) {
+      apply_sdir(M, u, V[j].data(), w.data(), 1);
+      for (int i = 0; i < meff[r]; ++i) O[((size_t)r * maxM + i) * maxM + j] = dot(V[i], w);
+    }
+  }
+  if (fail) return -1;
+  int rc = oracle_ftlm_sums(R, maxM, meff.data(), alpha.data(), beta.data(), reinterpret_cast<double*>(p.data()),
+                            (double)M.dim, M.g, T, nT, lnZ, E, C, MB, MB_imag, E0);
+  if (rc == 0)
+    rc = oracle_sftlm_sums(R, maxM, meff.data(), alpha.data(), beta.data(), reinterpret_cast<double*>(O.data()), M.g,
+                           T, nT, MB_sym, MB_sym_imag);
+  if (alpha_out) std::memcpy(alpha_out, alpha.data(), sizeof(double) * alpha.size());
+  if (beta_out) std::memcpy(beta_out, beta.data(), sizeof(double) * beta.size());
+  if (Omat_out) std::memcpy(Omat_out, O.data(), sizeof(cplx) * O.size());
   if (meff_out) std::memcpy(meff_out, meff.data(), sizeof(int) * meff.size());
   return rc;
 }
