@@ -319,7 +319,39 @@ def extra_workloads(F, T, stream, args):
     s.close()
     out["time_reversed_pairs"] = time_reversal_leg(F, T, stream)
     out["mn9_powder"] = mn9_leg(F, T, stream, args)
+    out["mn9_symmetric"] = sftlm_leg(F, T, stream)
     return out
+
+
+def sftlm_leg(F, T, stream):
+    """Symmetric FTLM (Eqs. E-2-G, E-2-H) on the Mn9-like system along one
+    dodecahedron direction: the run with its Lanczos vectors kept, then
+    O_ij = <v_i|u.S|v_j> on the device; against the plain run of the same
+    vectors."""
+    import torch
+    spec = W.WORKLOADS["mn9_powder"]
+    w = spec["system"]()[0]
+    s = F.System.from_dict(w)
+    R, M = spec["R"], spec["M"]
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, start="pairs")
+    times = {}
+    for sym in (False, True):
+        F.run(s, symmetric=sym, **kw)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = F.run(s, symmetric=sym, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[sym] = (e0.elapsed_time(e1), res)
+    ms_sym, res = times[True]
+    d = int(s.dim)
+    s.close()
+    return {"value": d * R * M / (ms_sym / 1e3), "unit": UNIT, "ms_per_run": ms_sym, "plain_ms_per_run": times[False][0],
+            "sym_ms": res["sym_ms"], "overhead": ms_sym / times[False][0], "R": R, "M": M, "d": d,
+            "stored_vector_bytes": d * R * M * 8,
+            "M_B_sym_minus_M_B_at_T": {f"{T[i]:.3g}": float(res["M_B_sym"][i] - res["M_B"][i]) for i in (0, 20, 39)},
+            "note": "states x vectors/s of the whole symmetric run; O formed from the stored Lanczos vectors"}
 
 
 def mn9_leg(F, T, stream, args):

@@ -216,6 +216,9 @@ typedef struct {
   int autotune;          /* 1 = time launch shapes on first use and keep the fastest */
   int time_kernels;      /* 1 = record device time of every H.v launch into the result */
   void* stream;          /* cudaStream_t the run is ordered with; NULL = default stream */
+  int symmetric;         /* 1 = also the symmetric estimator of M_B (sFTLM, Eqs. E-2-G/H):
+                            keeps all M Lanczos vectors on the device (M x R x dim values of
+                            dtype), forms O_ij = <v_i|u.S|v_j> per vector; one system only */
 } ftlm_run_params;
 
 typedef struct {
@@ -246,6 +249,12 @@ typedef struct {
   int grid;               /* CTAs per H.v launch */
   int threads;            /* threads per CTA */
   int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..7) */
+  /* symmetric runs (params.symmetric = 1); caller-allocated, may be NULL */
+  double* M_B_sym;        /* [nT] sFTLM: -g sum_r <r|e^{-bH/2} u.S e^{-bH/2}|r> / sum_r <r|e^{-bH}|r>,
+                             Eq. (E-2-G) with (E-2-H), shifted by E0 */
+  double* M_B_sym_imag;   /* [nT] imaginary part of that numerator, a diagnostic */
+  double* O_lanczos;      /* [R][M][M][2] complex O_ij = <v_i|u.S|v_j> (row-major; zero beyond M_eff) */
+  double sym_ms;          /* device time of forming O (after the Lanczos run) */
 } ftlm_result;
 
 /*
@@ -281,6 +290,19 @@ ftlm_status ftlm_run_batch(int n, const ftlm_system* const* systems, const ftlm_
  */
 ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,
                       double dim, double g, const double* T, int nT, ftlm_result* res);
+
+/*
+ * ftlm_sums_sym -- the host half of the symmetric estimator, Eqs. (E-2-G)
+ * and (E-2-H), on its own: from the tridiagonal data and the matrices
+ * O_ij = <v_i|u.S|v_j> of R runs (as returned in ftlm_result.O_lanczos),
+ * M_B_sym[t] and M_B_sym_imag[t] (may be NULL).  E0 is the lowest Ritz
+ * value over the R runs, as in ftlm_sums, so vectors run on several
+ * processes merge by concatenation.  Host-only: needs no GPU.
+ *  Omat  [R][M][M][2] complex, row-major per run.
+ */
+ftlm_status ftlm_sums_sym(int R, int M, const int* M_eff, const double* alpha, const double* beta,
+                          const double* Omat, double g, const double* T, int nT, double* M_B_sym,
+                          double* M_B_sym_imag);
 
 /*
  * ftlm_tune_shape -- overrides the launch shape that ftlm_apply_h, ftlm_run

@@ -44,6 +44,7 @@ class RunParams(ctypes.Structure):
         ("user_start", ctypes.c_void_p), ("T", ctypes.POINTER(ctypes.c_double)), ("nT", ctypes.c_int),
         ("obs_dir", ctypes.POINTER(ctypes.c_double)), ("breakdown_tol", ctypes.c_double),
         ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("symmetric", ctypes.c_int),
     ]
 
 
@@ -59,6 +60,8 @@ class Result(ctypes.Structure):
         ("cube_bits", ctypes.c_int), ("passes", ctypes.c_int), ("group_vectors", ctypes.c_int),
         ("tile_rows", ctypes.c_int),
         ("grid", ctypes.c_int), ("threads", ctypes.c_int), ("vector_major", ctypes.c_int),
+        ("M_B_sym", ctypes.POINTER(ctypes.c_double)), ("M_B_sym_imag", ctypes.POINTER(ctypes.c_double)),
+        ("O_lanczos", ctypes.POINTER(ctypes.c_double)), ("sym_ms", ctypes.c_double),
     ]
 
 
@@ -66,7 +69,7 @@ class Result(ctypes.Structure):
 EXPORTS = ["ftlm_system_create", "ftlm_system_destroy", "ftlm_system_dim", "ftlm_system_table_bytes",
            "ftlm_apply_h", "ftlm_apply_sdir",
            "ftlm_start_block", "ftlm_start_block_noalloc", "ftlm_start_pairs", "ftlm_time_reverse",
-           "ftlm_run", "ftlm_run_batch", "ftlm_sums",
+           "ftlm_run", "ftlm_run_batch", "ftlm_sums", "ftlm_sums_sym",
            "ftlm_tune_shape", "ftlm_last_error", "ftlm_version"]
 
 _lib = None
@@ -102,6 +105,7 @@ def lib():
         L.ftlm_run.argtypes = [vp, P(RunParams), P(Result)]
         L.ftlm_run_batch.argtypes = [i, P(vp), P(RunParams), P(Result)]
         L.ftlm_sums.argtypes = [i, i, P(i), pd, pd, pd, d, d, pd, i, P(Result)]
+        L.ftlm_sums_sym.argtypes = [i, i, P(i), pd, pd, pd, d, pd, i, pd, pd]
         L.ftlm_tune_shape.argtypes = [vp, i, i, i, i, i, i]
         L.ftlm_last_error.restype = ctypes.c_char_p
         L.ftlm_version.restype = ctypes.c_char_p
@@ -243,7 +247,7 @@ def start_block_noalloc(sys: System, out, nvec: int, seed: int, vec_offset: int 
 
 
 def _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, obs_dir, breakdown_tol, autotune,
-            time_kernels, stream, keep):
+            time_kernels, stream, keep, symmetric=False):
     T = _f64(T)
     od = _f64(obs_dir)
     keep += [T, od]
@@ -252,16 +256,22 @@ def _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, o
         else int(start)
     return RunParams(int(R), int(M), int(seed), int(vec_offset), _DTYPES[dtype], mode, int(basis_offset),
                      _ptr(user_start), _pd(T), len(T), _pd(od), float(breakdown_tol), int(autotune),
-                     int(time_kernels), _stream(stream, user_start))
+                     int(time_kernels), _stream(stream, user_start), int(bool(symmetric)))
 
 
-def _result(R, M, nT, keep):
+def _result(R, M, nT, keep, symmetric=False):
     out = {k: np.zeros(nT) for k in ("lnZ", "E", "C", "M_B", "M_B_imag")}
     out.update(alpha=np.zeros((R, M)), beta=np.zeros((R, M)), p=np.zeros((R, M), dtype=np.complex128),
                M_eff=np.zeros(R, dtype=np.int32))
+    if symmetric:
+        out.update(M_B_sym=np.zeros(nT), M_B_sym_imag=np.zeros(nT), O=np.zeros((R, M, M), dtype=np.complex128))
     keep.append(out)
     r = Result(*[_pd(out[k]) for k in ("lnZ", "E", "C", "M_B", "M_B_imag", "alpha", "beta")],
                _pd(out["p"].view(np.float64)), out["M_eff"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if symmetric:
+        r.M_B_sym = _pd(out["M_B_sym"])
+        r.M_B_sym_imag = _pd(out["M_B_sym_imag"])
+        r.O_lanczos = _pd(out["O"].view(np.float64))
     return r, out
 
 
@@ -271,18 +281,22 @@ def _finish(r, out):
                shape={"cube_bits": r.cube_bits, "passes": r.passes, "group_vectors": r.group_vectors,
                       "tile_rows": r.tile_rows,
                       "grid": r.grid, "threads": r.threads, "vector_major": r.vector_major})
+    if "M_B_sym" in out:
+        out["sym_ms"] = r.sym_ms
     return out
 
 
 def run(sys: System, R: int, M: int, T, seed: int = 0, vec_offset: int = 0, dtype="c64", start="random",
         basis_offset: int = 0, user_start=None, obs_dir=None, breakdown_tol: float = 0.0, autotune=False,
-        time_kernels=False, stream=None) -> dict:
-    """Plain FTLM (``ftlm_run``): returns lnZ, E, C, M_B, M_B_imag per T, E0,
-    and the per-vector alpha, beta, p, M_eff."""
+        time_kernels=False, stream=None, symmetric=False) -> dict:
+    """FTLM (``ftlm_run``): returns lnZ, E, C, M_B, M_B_imag per T, E0, and the
+    per-vector alpha, beta, p, M_eff; with symmetric=True also the symmetric
+    estimator M_B_sym, M_B_sym_imag (Eqs. E-2-G, E-2-H), the matrices
+    O[r, i, j] = <v_i|u.S|v_j> and sym_ms."""
     keep = []
     p = _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, obs_dir, breakdown_tol, autotune,
-                time_kernels, stream, keep)
-    r, out = _result(R, M, p.nT, keep)
+                time_kernels, stream, keep, symmetric)
+    r, out = _result(R, M, p.nT, keep, symmetric)
     _check(lib().ftlm_run(sys.handle, ctypes.byref(p), ctypes.byref(r)))
     return _finish(r, out)
 
@@ -322,6 +336,21 @@ def sums(alpha, beta, p, M_eff, dim, g, T) -> dict:
                            _pd(pc.view(np.float64)), float(dim), float(g), _pd(T), len(T), ctypes.byref(r)))
     out["E0"] = r.E0
     return out
+
+
+def sums_sym(alpha, beta, O, M_eff, g, T):
+    """Host-only symmetric estimator from per-vector data (``ftlm_sums_sym``):
+    returns (M_B_sym, M_B_sym_imag)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    R, M = a.shape
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    Oc = np.ascontiguousarray(O, dtype=np.complex128)
+    me = np.ascontiguousarray(M_eff, dtype=np.int32)
+    T = _f64(T)
+    mb, mbi = np.zeros(len(T)), np.zeros(len(T))
+    _check(lib().ftlm_sums_sym(R, M, me.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _pd(a), _pd(b),
+                               _pd(Oc.view(np.float64)), float(g), _pd(T), len(T), _pd(mb), _pd(mbi)))
+    return mb, mbi
 
 
 def tune_shape(sys: System, nvec: int, dtype="c64", cube_bits: int = 0, group_vectors: int = 1,

@@ -2,6 +2,7 @@
 // and start-block entry points, and the FTLM driver (arxiv 2607.25585,
 // Eqs. 4-5 and Sec. II.C): start block, M Lanczos steps captured in one CUDA
 // graph, then the host eigensolve and Boltzmann sums.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,6 +84,7 @@ struct ftlm_system {
   DevBuf A, B, U, scal;  // Lanczos workspace: two vector blocks, the observable block, scalars
   DevBuf Hq;             // H q_j when the gather and the step epilogue are separate launches
   DevBuf ep, ecnt, esc;  // start-block scratch: partials, arrival counter, scalars
+  DevBuf Vs, Wc, Od;     // symmetric runs: stored Lanczos vectors, u.S chunk, O matrices
   std::mutex mu;
 };
 
@@ -510,6 +512,7 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
            (unsigned long long)p->basis_offset, p->user_start, p->time_kernels, pl.sh.threads, pl.sh.rows_per_tile,
            pl.grid, p->breakdown_tol, u[0], u[1], u[2], p->obs_dir ? 1 : 0, p->stream);
   k += buf;
+  k += p->symmetric ? "|sym" : "";
   snprintf(buf, sizeof buf, "|half%d vm%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
            pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
   return k + buf;
@@ -531,6 +534,8 @@ ftlm_status validate_params(const ftlm_run_params* p, const std::vector<ftlm_sys
     return fail(FTLM_ERR_INVALID_ARG, "user_start must be 16-byte aligned");
   if (p->start == FTLM_START_USER && sys.size() != 1)
     return fail(FTLM_ERR_INVALID_ARG, "user start vectors need a single system");
+  if (p->symmetric && sys.size() != 1) return fail(FTLM_ERR_INVALID_ARG, "symmetric runs take one system");
+  if (p->symmetric != 0 && p->symmetric != 1) return fail(FTLM_ERR_INVALID_ARG, "symmetric must be 0 or 1");
   if (!(p->breakdown_tol >= 0) || !std::isfinite(p->breakdown_tol))
     return fail(FTLM_ERR_INVALID_ARG, "breakdown_tol must be finite and >= 0");
   if (p->obs_dir && !(std::isfinite(p->obs_dir[0]) && std::isfinite(p->obs_dir[1]) && std::isfinite(p->obs_dir[2])))
@@ -543,7 +548,11 @@ ftlm_status validate_params(const ftlm_run_params* p, const std::vector<ftlm_sys
   return FTLM_OK;
 }
 
-size_t staged_bytes(int R, int M) { return sizeof(double) * ((size_t)M * R * 4) + sizeof(int) * (size_t)R; }
+// Staged per system: alpha, beta, p ([M][R], [M][R], [M][R][2]) and sigma ([M][R],
+// the scale of the unnormalised Lanczos vectors), contiguous in the scalars;
+// then M_eff [R].
+size_t staged_doubles(int R, int M) { return (size_t)M * R * 5; }
+size_t staged_bytes(int R, int M) { return sizeof(double) * staged_doubles(R, M) + sizeof(int) * (size_t)R; }
 
 // Enqueues one whole run on `st` (which the caller is capturing).
 ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const ftlm_run_params* p, const Plan& pl,
@@ -597,6 +606,15 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
     a.inst = (j % 2 == 0) ? d_even : d_odd;
     a.step = j;
     a.first = j == 0;
+    if (p->symmetric) {  // keep q_j (vector-major) for the matrix of u.S in the Lanczos basis
+      ftlm_system* s0 = sys[0];
+      const size_t vb = (size_t)s0->hs.dim * R * (c64 ? 8 : 16);
+      const void* q = (j % 2 == 0) ? s0->A.p : s0->B.p;
+      void* dst = static_cast<char*>(s0->Vs.p) + vb * j;
+      if (pl.half.vm) CK(cudaMemcpyAsync(dst, q, vb, cudaMemcpyDeviceToDevice, st));
+      else CKI(launch_to_vector_major(q, dst, (long long)s0->hs.dim, R, c64, st));
+      ctx.launches++;
+    }
     if (split) {
       LaunchArgs g = a;
       g.inst = (j % 2 == 0) ? d_gather_even : d_gather_odd;
@@ -634,8 +652,9 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   for (int k = 0; k < n; ++k) {  // alpha, beta, p, M_eff -> pinned host staging
     DevScalars sc = scalars_at(sys[k]->scal.p, R, M);
     char* dst = ctx.pinned + per * k;
-    CK(cudaMemcpyAsync(dst, sc.alpha, sizeof(double) * (size_t)M * R * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(dst + sizeof(double) * (size_t)M * R * 4, sc.meff, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dst, sc.alpha, sizeof(double) * staged_doubles(R, M), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dst + sizeof(double) * staged_doubles(R, M), sc.meff, sizeof(int) * R, cudaMemcpyDeviceToHost,
+                       st));
   }
   return FTLM_OK;
 }
@@ -708,6 +727,104 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
   return FTLM_OK;
 }
 
+// ---- symmetric estimator: O_ij = <v_i|u.S|v_j> per vector ---------------------
+
+std::mutex g_blas_mu;
+cublasHandle_t g_blas[64] = {};  // one cuBLAS handle per device, created on first use
+
+cublasHandle_t blas_handle() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_blas_mu);
+  if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
+  return g_blas[dev];
+}
+
+// After a symmetric run: G_r = Q_r^H (u.S Q_r) for the stored unnormalised
+// vectors Q_r = [q_0 .. q_{M-1}] of every vector r, row chunk by row chunk (the
+// u.S kernel writes a chunk of u.S Q, a strided-batched complex GEMM adds its
+// share to G_r), then O_ij = sigma_i sigma_j G_ij on the host.  Omat [R][M][M]
+// complex row-major; sigma [M][R].
+ftlm_status symmetric_matrices(ftlm_system* s, const ftlm_run_params* p, cudaStream_t st, const double* sigma,
+                               std::vector<double>& Omat, double& ms) {
+  const int R = p->R, M = p->M, c64 = p->dtype == FTLM_C64;
+  const long long d = (long long)s->hs.dim;
+  const size_t esz = c64 ? 8 : 16;
+  const long long nv = (long long)M * R;
+  if ((long long)R * d >= (1ll << 31)) return fail(FTLM_ERR_UNSUPPORTED, "R * dim must be below 2^31 for symmetric runs");
+  long long rows = std::max<long long>(256, (256ll << 20) / (nv * (long long)esz));
+  rows = std::min<long long>(rows, d);
+  if (s->Wc.bytes < (size_t)(nv * rows) * esz) {
+    s->Wc.release();
+    if (s->Wc.ensure((size_t)(nv * rows) * esz) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "u.S chunk");
+  }
+  const size_t obytes = (size_t)R * M * M * esz;
+  if (s->Od.bytes < obytes) {
+    s->Od.release();
+    if (s->Od.ensure(obytes) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "O matrices");
+  }
+  cublasHandle_t h = blas_handle();
+  if (!h) return fail(FTLM_ERR_CUDA, "cuBLAS handle");
+  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(FTLM_ERR_CUDA, "cublasSetStream");
+  InstDesc hd = base_desc(s, c64);
+  observable_coefs(s->hs, p->obs_dir, hd.obs);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  for (long long c0 = 0; c0 < d; c0 += rows) {
+    const int cnt = (int)std::min<long long>(rows, d - c0);
+    CKI(launch_sdir_vm(&hd, s->Vs.p, s->Wc.p, (int)nv, c0, cnt, (int)rows, c64, st));
+    // G_r (M x M, column-major) (+)= A_r^H B_r with A_r = Q_r[c0 : c0 + cnt, :] (column j
+    // at Vs + (j R + r) d + c0, so lda = R d, batch stride d) and B_r the chunk of u.S Q_r
+    // (column j at Wc + (j R + r) rows, ldb = R rows, batch stride rows)
+    cublasStatus_t bs;
+    if (c64) {
+      const cuComplex one = make_cuComplex(1.f, 0.f), beta = make_cuComplex(c0 == 0 ? 0.f : 1.f, 0.f);
+      bs = cublasCgemmStridedBatched(h, CUBLAS_OP_C, CUBLAS_OP_N, M, M, cnt, &one,
+                                     reinterpret_cast<const cuComplex*>(s->Vs.p) + c0, (int)(R * d), d,
+                                     reinterpret_cast<const cuComplex*>(s->Wc.p), (int)(R * rows), rows, &beta,
+                                     reinterpret_cast<cuComplex*>(s->Od.p), M, (long long)M * M, R);
+    } else {
+      const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), beta = make_cuDoubleComplex(c0 == 0 ? 0.0 : 1.0, 0.0);
+      bs = cublasZgemmStridedBatched(h, CUBLAS_OP_C, CUBLAS_OP_N, M, M, cnt, &one,
+                                     reinterpret_cast<const cuDoubleComplex*>(s->Vs.p) + c0, (int)(R * d), d,
+                                     reinterpret_cast<const cuDoubleComplex*>(s->Wc.p), (int)(R * rows), rows, &beta,
+                                     reinterpret_cast<cuDoubleComplex*>(s->Od.p), M, (long long)M * M, R);
+    }
+    if (bs != CUBLAS_STATUS_SUCCESS) return fail(FTLM_ERR_CUDA, "cuBLAS batched GEMM failed (" + std::to_string((int)bs) + ")");
+  }
+  CK(cudaEventRecord(e1, st));
+  std::vector<char> host(obytes);
+  CK(cudaMemcpyAsync(host.data(), s->Od.p, obytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float fms = 0.f;
+  CK(cudaEventElapsedTime(&fms, e0, e1));
+  ms = fms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  Omat.assign((size_t)R * M * M * 2, 0.0);
+  for (int r = 0; r < R; ++r)
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        const size_t src = (size_t)r * M * M + (size_t)j * M + i;  // column-major G_r(i, j)
+        double gr, gi;
+        if (c64) {
+          const float* f = reinterpret_cast<const float*>(host.data()) + 2 * src;
+          gr = f[0];
+          gi = f[1];
+        } else {
+          const double* f = reinterpret_cast<const double*>(host.data()) + 2 * src;
+          gr = f[0];
+          gi = f[1];
+        }
+        const double sc = sigma[(size_t)i * R + r] * sigma[(size_t)j * R + r];
+        Omat[(((size_t)r * M + i) * M + j) * 2] = sc * gr;
+        Omat[(((size_t)r * M + i) * M + j) * 2 + 1] = sc * gi;
+      }
+  return FTLM_OK;
+}
+
 ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ftlm_result* res) {
   ftlm_status vs = validate_params(p, sys);
   if (vs != FTLM_OK) return vs;
@@ -730,6 +847,16 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   if (pl.half.on) {
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, pl.half.vm ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
+  }
+  if (p->symmetric) {  // the M Lanczos vectors of every vector
+    ftlm_system* s0 = sys[0];
+    const size_t vb = (size_t)s0->hs.dim * R * (c64 ? 8 : 16) * M;
+    if (s0->Vs.bytes < vb) {
+      s0->Vs.release();
+      if (s0->Vs.ensure(vb) != cudaSuccess)
+        return fail(FTLM_ERR_OUT_OF_MEMORY, "symmetric run: " + std::to_string(vb) + " bytes of Lanczos vectors");
+      s0->gen++;
+    }
   }
   const std::string key = run_key(sys, p, pl);
   RunCtx* ctx = nullptr;
@@ -775,7 +902,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     const double* alpha_d = reinterpret_cast<const double*>(src);  // [M][R]
     const double* beta_d = alpha_d + (size_t)M * R;
     const double* p_d = beta_d + (size_t)M * R;                     // [M][R][2]
-    const int* meff = reinterpret_cast<const int*>(src + sizeof(double) * (size_t)M * R * 4);
+    const int* meff = reinterpret_cast<const int*>(src + sizeof(double) * staged_doubles(R, M));
     std::vector<double> al((size_t)R * M), be((size_t)R * M), pp((size_t)R * M * 2);
     for (int r = 0; r < R; ++r)
       for (int j = 0; j < M; ++j) {
@@ -809,6 +936,22 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     out.grid = pl.half.on ? pl.half.grid : pl.grid;
     out.threads = pl.half.on ? pl.half.threads : pl.sh.threads;
     out.vector_major = pl.half.vm ? 1 : 0;
+    out.sym_ms = 0.0;
+    if (p->symmetric) {  // Eqs. (E-2-G), (E-2-H)
+      const double* sigma_d = p_d + (size_t)M * R * 2;  // [M][R]
+      std::vector<double> Omat;
+      double sms = 0.0;
+      ftlm_status os = symmetric_matrices(sys[k], p, st, sigma_d, Omat, sms);
+      if (os != FTLM_OK) return os;
+      out.sym_ms = sms;
+      if (out.M_B_sym) {
+        std::string m2;
+        ftlm_status hs2 = host_sums_sym(R, M, me.data(), al.data(), be.data(), Omat.data(), sys[k]->hs.g, p->T,
+                                        p->nT, out.M_B_sym, out.M_B_sym_imag, m2);
+        if (hs2 != FTLM_OK) return fail(hs2, m2);
+      }
+      if (out.O_lanczos) std::memcpy(out.O_lanczos, Omat.data(), sizeof(double) * Omat.size());
+    }
   }
   return FTLM_OK;
 }
@@ -1260,6 +1403,17 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
   ftlm_status s = host_sums(R, M, M_eff, alpha, beta, p, dim, g, T, nT, res, msg);
   if (s != FTLM_OK) return fail(s, msg);
   return FTLM_OK;
+}
+
+ftlm_status ftlm_sums_sym(int R, int M, const int* M_eff, const double* alpha, const double* beta,
+                          const double* Omat, double g, const double* T, int nT, double* M_B_sym,
+                          double* M_B_sym_imag) {
+  if (!M_B_sym) return fail(FTLM_ERR_INVALID_ARG, "M_B_sym is NULL");
+  for (int t = 0; T && t < nT; ++t)
+    if (!(T[t] > 0.0) || !std::isfinite(T[t])) return fail(FTLM_ERR_INVALID_ARG, "temperatures must be > 0");
+  std::string msg;
+  ftlm_status s = host_sums_sym(R, M, M_eff, alpha, beta, Omat, g, T, nT, M_B_sym, M_B_sym_imag, msg);
+  return s == FTLM_OK ? FTLM_OK : fail(s, msg);
 }
 
 const char* ftlm_last_error(void) { return g_err.c_str(); }

@@ -182,6 +182,9 @@ int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int
 int launch_start_pairs(const InstDesc* h, int R, uint64_t seed, uint64_t vec_offset, void* out, int c64,
                        void* stream, int vector_major);
 int launch_time_reverse(const InstDesc* h, const void* x, void* y, int R, int c64, void* stream);
+// W[k][t] = (u.S V_k)[c0 + t], t < cnt, for nv vector-major vectors V_k (h->obs = u)
+int launch_sdir_vm(const InstDesc* h, const void* V, void* W, int nv, long long c0, int cnt, int T, int c64,
+                   void* stream);
 int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
 size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads);
 int prepare_rows_kernels(size_t smem);
@@ -208,8 +211,12 @@ int vm_max_ctas_per_sm(int K, int min_blocks, int c64, int threads, size_t smem,
 int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream);
 constexpr int kVmLaneBits = 5;  // rows per warp-wide load: 2^5
 
-// Host tridiagonal eigensolver + sums (tridiag.cpp).
+// Host tridiagonal eigensolver + sums (tridiag.cpp); host_sums_sym: the
+// symmetric estimator of M_B from the matrices O_ij = <v_i|u.S|v_j>.
 ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,
                       double dim, double g, const double* T, int nT, ftlm_result* res, std::string& msg);
+ftlm_status host_sums_sym(int R, int M, const int* M_eff, const double* alpha, const double* beta,
+                          const double* Omat, double g, const double* T, int nT, double* MB_sym, double* MB_sym_imag,
+                          std::string& msg);
 
 }  // namespace ftlm

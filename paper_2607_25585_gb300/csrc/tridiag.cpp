@@ -151,4 +151,77 @@ ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const
   return FTLM_OK;
 }
 
+// Symmetric FTLM for O = u.S, Eqs. (E-2-G), (E-2-H): per run,
+//   num_r = sum_{m,n} e^{-beta (eps_m + eps_n)/2} U_0m <m|O|n> U_0n = y^T O y,
+//   y_i = sum_n U_in e^{-beta eps_n / 2} U_0n,
+// with O_ij = <v_i|O|v_j> in the Lanczos basis (<m|O|n> = (U^T O U)_mn, U real),
+// den_r = sum_n e^{-beta eps_n} U_0n^2; both shifted by E0, the lowest Ritz value
+// over all runs.  Omat[r][i][j] (complex, row-major, M x M per run).  The whole
+// of U is accumulated here: O(M^3) per run.
+ftlm_status host_sums_sym(int R, int M, const int* M_eff, const double* alpha, const double* beta,
+                          const double* Omat, double g, const double* T, int nT, double* MB_sym, double* MB_sym_imag,
+                          std::string& msg) {
+  if (R < 1 || M < 1 || !M_eff || !alpha || !beta || !Omat || !T || nT < 1) {
+    msg = "sFTLM sums: invalid arguments";
+    return FTLM_ERR_INVALID_ARG;
+  }
+  struct Run {
+    int m = 0;
+    std::vector<double> eps, U;  // U[k * m + n] = U_kn
+  };
+  std::vector<Run> runs(R);
+  double E0 = std::numeric_limits<double>::infinity();
+  for (int r = 0; r < R; ++r) {
+    Run& run = runs[r];
+    const int m = run.m = M_eff[r];
+    if (m < 1 || m > M) {
+      msg = "M_eff out of range";
+      return FTLM_ERR_INVALID_ARG;
+    }
+    run.eps.assign(alpha + (size_t)r * M, alpha + (size_t)r * M + m);
+    std::vector<double> e(m > 1 ? m - 1 : 1, 0.0);
+    for (int j = 0; j + 1 < m; ++j) e[j] = beta[(size_t)r * M + j];
+    run.U.assign((size_t)m * m, 0.0);
+    std::vector<double*> rows(m);
+    for (int k = 0; k < m; ++k) {
+      run.U[(size_t)k * m + k] = 1.0;
+      rows[k] = run.U.data() + (size_t)k * m;
+    }
+    if (!ql_implicit(m, run.eps.data(), e.data(), m, rows.data())) {
+      msg = "tridiagonal eigensolver did not converge (run " + std::to_string(r) + ")";
+      return FTLM_ERR_NUMERICAL;
+    }
+    for (int n = 0; n < m; ++n) E0 = std::min(E0, run.eps[n]);
+  }
+  for (int t = 0; t < nT; ++t) {
+    const double b = 1.0 / T[t];
+    double den = 0.0, nre = 0.0, nim = 0.0;
+    for (int r = 0; r < R; ++r) {
+      const Run& run = runs[r];
+      const int m = run.m;
+      std::vector<double> x(m), y(m, 0.0);
+      for (int n = 0; n < m; ++n) {
+        const double h = std::exp(-0.5 * b * (run.eps[n] - E0));
+        x[n] = h * run.U[n];  // U_0n
+        den += h * h * run.U[n] * run.U[n];
+      }
+      for (int i = 0; i < m; ++i) {
+        double acc = 0.0;
+        for (int n = 0; n < m; ++n) acc += run.U[(size_t)i * m + n] * x[n];
+        y[i] = acc;
+      }
+      const double* O = Omat + (size_t)r * M * M * 2;
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+          const double w = y[i] * y[j];
+          nre += w * O[((size_t)i * M + j) * 2];
+          nim += w * O[((size_t)i * M + j) * 2 + 1];
+        }
+    }
+    MB_sym[t] = -g * nre / den;
+    if (MB_sym_imag) MB_sym_imag[t] = -g * nim / den;
+  }
+  return FTLM_OK;
+}
+
 }  // namespace ftlm

@@ -71,3 +71,15 @@ def test_sums_reject_bad_input():
         F.sums(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)), [4], 8, 2.0, [1.0])
     with pytest.raises(F.FtlmError):
         F.sums(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)), [2], 8, 2.0, [0.0])
+
+
+def test_sums_sym_match_oracle(rng):
+    """ftlm_sums_sym (host-only) reproduces the oracle's symmetric estimator
+    from the same per-vector data."""
+    from conftest import random_system, oracle_system
+    w = random_system(rng, [1, 2, 1, 1])
+    T = np.array([0.1, 0.5, 2.0, 10.0])
+    o = oracle.sftlm(oracle_system(w), R=3, M=12, T=T, seed=3)
+    mb, mbi = F.sums_sym(o["alpha"], o["beta"], o["O"], o["M_eff"], w["g"], T)
+    assert np.allclose(mb, o["M_B_sym"], rtol=1e-11, atol=1e-13)
+    assert np.allclose(mbi, o["M_B_sym_imag"], rtol=1e-9, atol=1e-12)
