@@ -320,6 +320,49 @@ def extra_workloads(F, T, stream, args):
     out["time_reversed_pairs"] = time_reversal_leg(F, T, stream)
     out["mn9_powder"] = mn9_leg(F, T, stream, args)
     out["mn9_symmetric"] = sftlm_leg(F, T, stream)
+    out["stored_matrix"] = stored_matrix_leg(F, stream)
+    return out
+
+
+def stored_matrix_leg(F, stream):
+    """The stored-matrix comparison path on the headline system: assembly
+    time and memory, and one H.v with the stored matrix against the
+    matrix-free ftlm_apply_h on the same row-major block (complex64 with
+    R = 64, and complex128 with R = 1 as in the plain FP64 path)."""
+    import time
+    import torch
+    spec = W.WORKLOADS[WORKLOAD]
+    s = F.System.from_dict(spec["system"]())
+    d = s.dim
+    out = {}
+    for dtype, R in (("c64", spec["R"]), ("c128", 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = F.CsrMatrix(s, dtype)
+        build_s = time.perf_counter() - t0
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        x = torch.randn(d, R, dtype=tdt, device="cuda")
+        y = torch.empty_like(x)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        res = {}
+        for name, fn in (("stored", lambda: m.apply(x, y, R, stream=stream)),
+                         ("matrix_free", lambda: F.apply_h(s, x, y, R, dtype, stream=stream))):
+            for _ in range(2):
+                fn()
+            e0.record(stream)
+            for _ in range(5):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / 5
+        out[f"{dtype}_R{R}"] = {"stored_ms": res["stored"], "matrix_free_ms": res["matrix_free"],
+                                "matrix_free_speedup": res["stored"] / res["matrix_free"], "nnz": m.nnz,
+                                "matrix_bytes": m.bytes, "build_s": build_s,
+                                "stored_gbs": (m.bytes + 2 * d * R * x.element_size()) / (res["stored"] / 1e3) / 1e9}
+        m.close()
+        del x, y
+    s.close()
     return out
 
 

@@ -292,6 +292,33 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
                       double dim, double g, const double* T, int nT, ftlm_result* res);
 
 /*
+ * Stored-matrix comparison path.  The paper keeps its Hamiltonian stripes
+ * stored on the GPUs in coordinate form, with the elements of one row handled
+ * by one thread (Sec. II.C, Table I); ftlm_csr is that matrix in compressed-row
+ * form on one device, so that the matrix-free ftlm_apply_h can be measured
+ * against it.
+ *
+ * ftlm_csr_create -- assembles H (Eq. 3) on the current device: the elements
+ * of every row as the matrix-free gather enumerates them (diagonal first),
+ * exact zeros dropped; row pointers int64 [dim + 1], columns int32 (dim must
+ * be below 2^31, else FTLM_ERR_UNSUPPORTED), values complex of dtype.
+ * Memory: 8 (dim + 1) + nnz (4 + 8 or 16) bytes (FTLM_ERR_OUT_OF_MEMORY if it
+ * does not fit).  Blocks until assembled.  The matrix does not refer to sys
+ * afterwards.
+ */
+typedef struct ftlm_csr ftlm_csr;
+ftlm_status ftlm_csr_create(const ftlm_system* sys, ftlm_dtype dtype, ftlm_csr** out);
+uint64_t ftlm_csr_nnz(const ftlm_csr* m);    /* stored elements; 0 for NULL */
+uint64_t ftlm_csr_bytes(const ftlm_csr* m);  /* device bytes held; 0 for NULL */
+/*
+ * ftlm_csr_apply -- y = H x with the stored matrix; x, y device blocks
+ * [dim][nvec] of the matrix's dtype, 16-byte aligned, not overlapping; nvec
+ * as for ftlm_apply_h.  Asynchronous on stream (NULL = default stream).
+ */
+ftlm_status ftlm_csr_apply(const ftlm_csr* m, const void* x, void* y, int nvec, void* stream);
+void ftlm_csr_destroy(ftlm_csr* m);
+
+/*
  * ftlm_sums_sym -- the host half of the symmetric estimator, Eqs. (E-2-G)
  * and (E-2-H), on its own: from the tridiagonal data and the matrices
  * O_ij = <v_i|u.S|v_j> of R runs (as returned in ftlm_result.O_lanczos),

@@ -70,6 +70,7 @@ EXPORTS = ["ftlm_system_create", "ftlm_system_destroy", "ftlm_system_dim", "ftlm
            "ftlm_apply_h", "ftlm_apply_sdir",
            "ftlm_start_block", "ftlm_start_block_noalloc", "ftlm_start_pairs", "ftlm_time_reverse",
            "ftlm_run", "ftlm_run_batch", "ftlm_sums", "ftlm_sums_sym",
+           "ftlm_csr_create", "ftlm_csr_nnz", "ftlm_csr_bytes", "ftlm_csr_apply", "ftlm_csr_destroy",
            "ftlm_tune_shape", "ftlm_last_error", "ftlm_version"]
 
 _lib = None
@@ -106,6 +107,14 @@ def lib():
         L.ftlm_run_batch.argtypes = [i, P(vp), P(RunParams), P(Result)]
         L.ftlm_sums.argtypes = [i, i, P(i), pd, pd, pd, d, d, pd, i, P(Result)]
         L.ftlm_sums_sym.argtypes = [i, i, P(i), pd, pd, pd, d, pd, i, pd, pd]
+        L.ftlm_csr_create.argtypes = [vp, i, P(vp)]
+        L.ftlm_csr_nnz.restype = ctypes.c_uint64
+        L.ftlm_csr_nnz.argtypes = [vp]
+        L.ftlm_csr_bytes.restype = ctypes.c_uint64
+        L.ftlm_csr_bytes.argtypes = [vp]
+        L.ftlm_csr_apply.argtypes = [vp, vp, vp, i, vp]
+        L.ftlm_csr_destroy.argtypes = [vp]
+        L.ftlm_csr_destroy.restype = None
         L.ftlm_tune_shape.argtypes = [vp, i, i, i, i, i, i]
         L.ftlm_last_error.restype = ctypes.c_char_p
         L.ftlm_version.restype = ctypes.c_char_p
@@ -336,6 +345,33 @@ def sums(alpha, beta, p, M_eff, dim, g, T) -> dict:
                            _pd(pc.view(np.float64)), float(dim), float(g), _pd(T), len(T), ctypes.byref(r)))
     out["E0"] = r.E0
     return out
+
+
+class CsrMatrix:
+    """H assembled as a stored sparse matrix on the device (``ftlm_csr_*``): the
+    comparison path for the matrix-free ``apply_h``."""
+
+    def __init__(self, sys: System, dtype="c64"):
+        h = ctypes.c_void_p()
+        _check(lib().ftlm_csr_create(sys.handle, _DTYPES[dtype], ctypes.byref(h)))
+        self.handle = h.value
+        self.dtype = dtype
+        self.nnz = int(lib().ftlm_csr_nnz(self.handle))
+        self.bytes = int(lib().ftlm_csr_bytes(self.handle))
+
+    def apply(self, x, y, nvec: int, stream=None):
+        _check(lib().ftlm_csr_apply(self.handle, _ptr(x), _ptr(y), int(nvec), _stream(stream, x)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ftlm_csr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sums_sym(alpha, beta, O, M_eff, g, T):

@@ -348,7 +348,7 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
     a.real_pm = pl.half.real_pm;
     a.min_blocks = pl.half.min_blocks;
-    a.inline_one = 0;
+    a.inline_one = (a.inline_one && pl.half.nvg == 1) ? 1 : 0;  // one vector: the descriptor by value
     a.single_pass = pl.half.passes == 1 ? 1 : 0;
     a.npass = pl.half.passes;  // pass p writes y + p * R * d (vector-major blocks)
     a.pass_stride = (long long)pl.half.nvg * pl.half.dim;
@@ -1082,8 +1082,14 @@ ftlm_status rows_entry(const ftlm_system* cs, int mode, const double* u, const v
   if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
   Plan pl;
   std::vector<ftlm_system*> one{s};
-  ftlm_status ps = make_plan(one, nvec, c64, pl);
+  // one vector: the row-major and the vector-major layouts coincide, so H.v may
+  // use the vector-major gather
+  ftlm_status ps = make_plan(one, nvec, c64, pl, nullptr, mode == kModeApply && nvec == 1);
   if (ps != FTLM_OK) return ps;
+  if (pl.half.vm && pl.half.passes > 1) {  // the multi-pass form writes one block per pass: not for a caller's y
+    ps = make_plan(one, nvec, c64, pl);
+    if (ps != FTLM_OK) return ps;
+  }
   LaunchArgs a = pl.base;
   a.inline_one = 1;
   a.one = base_desc(s, c64);
@@ -1404,6 +1410,84 @@ ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const
   if (s != FTLM_OK) return fail(s, msg);
   return FTLM_OK;
 }
+
+}  // extern "C"
+
+struct ftlm_csr {
+  int device = 0;
+  int c64 = 1;
+  long long dim = 0;
+  uint64_t nnz = 0;
+  DevBuf rp, col, val;
+};
+
+extern "C" {
+
+ftlm_status ftlm_csr_create(const ftlm_system* s, ftlm_dtype dtype, ftlm_csr** out) {
+  if (!s || !out) return fail(FTLM_ERR_INVALID_ARG, "system or out is NULL");
+  if (dtype != FTLM_C64 && dtype != FTLM_C128) return fail(FTLM_ERR_INVALID_ARG, "unknown dtype");
+  *out = nullptr;
+  const int c64 = dtype == FTLM_C64;
+  const long long dim = (long long)s->hs.dim;
+  if (dim >= (1ll << 31)) return fail(FTLM_ERR_UNSUPPORTED, "the stored matrix needs dim < 2^31 (32-bit columns)");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev != s->device) return fail(FTLM_ERR_INVALID_ARG, "system lives on another device");
+  auto m = std::make_unique<ftlm_csr>();
+  m->device = dev;
+  m->c64 = c64;
+  m->dim = dim;
+  LaunchArgs a;
+  a.inline_one = 1;
+  a.one = base_desc(s, c64);
+  a.n_inst = 1;
+  a.tab_reals = s->hs.lay.total;
+  a.max_n = s->hs.n;
+  const size_t smem = csr_smem_bytes(a, c64);
+  if (smem > 227 * 1024) return fail(FTLM_ERR_UNSUPPORTED, "coupling tables do not fit in shared memory");
+  CKI(csr_prepare(std::max<size_t>(smem, 48 * 1024)));
+  cudaStream_t st = s->own_stream;
+  DevBuf counts;
+  if (counts.ensure(sizeof(int) * (size_t)dim) != cudaSuccess || m->rp.ensure(sizeof(long long) * (size_t)(dim + 1)) != cudaSuccess)
+    return fail(FTLM_ERR_OUT_OF_MEMORY, "row pointers");
+  CKI(launch_csr_count(a, c64, smem, reinterpret_cast<int*>(counts.p), st));
+  CKI(csr_scan(reinterpret_cast<const int*>(counts.p), reinterpret_cast<long long*>(m->rp.p), dim, st));
+  long long nnz = 0;
+  CK(cudaMemcpyAsync(&nnz, reinterpret_cast<long long*>(m->rp.p) + dim, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  counts.release();
+  m->nnz = (uint64_t)nnz;
+  if (m->col.ensure(sizeof(int) * (size_t)nnz) != cudaSuccess || m->val.ensure((size_t)nnz * (c64 ? 8 : 16)) != cudaSuccess)
+    return fail(FTLM_ERR_OUT_OF_MEMORY, "stored matrix of " + std::to_string(nnz) + " elements");
+  CKI(launch_csr_fill(a, c64, smem, reinterpret_cast<const long long*>(m->rp.p), reinterpret_cast<int*>(m->col.p),
+                      m->val.p, st));
+  CK(cudaStreamSynchronize(st));
+  *out = m.release();
+  return FTLM_OK;
+}
+
+uint64_t ftlm_csr_nnz(const ftlm_csr* m) { return m ? m->nnz : 0; }
+
+uint64_t ftlm_csr_bytes(const ftlm_csr* m) {
+  return m ? m->rp.bytes + m->col.bytes + m->val.bytes : 0;
+}
+
+ftlm_status ftlm_csr_apply(const ftlm_csr* m, const void* x, void* y, int nvec, void* stream) {
+  if (!m) return fail(FTLM_ERR_INVALID_ARG, "matrix is NULL");
+  if (nvec < 1 || nvec > max_vectors(m->c64))
+    return fail(FTLM_ERR_INVALID_ARG, "nvec must be in 1.." + std::to_string(max_vectors(m->c64)));
+  if (!x || !y) return fail(FTLM_ERR_INVALID_ARG, "vector blocks must not be NULL");
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+    return fail(FTLM_ERR_INVALID_ARG, "vector blocks must be 16-byte aligned");
+  const size_t bytes = (size_t)m->dim * nvec * (m->c64 ? 8 : 16);
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+  if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
+  CKI(launch_csr_spmm(m->dim, nvec, reinterpret_cast<const long long*>(m->rp.p), reinterpret_cast<const int*>(m->col.p),
+                      m->val.p, x, y, m->c64, reinterpret_cast<cudaStream_t>(stream)));
+  return FTLM_OK;
+}
+
+void ftlm_csr_destroy(ftlm_csr* m) { delete m; }
 
 ftlm_status ftlm_sums_sym(int R, int M, const int* M_eff, const double* alpha, const double* beta,
                           const double* Omat, double g, const double* T, int nT, double* M_B_sym,

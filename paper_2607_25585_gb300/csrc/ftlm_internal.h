@@ -211,6 +211,16 @@ int vm_max_ctas_per_sm(int K, int min_blocks, int c64, int threads, size_t smem,
 int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream);
 constexpr int kVmLaneBits = 5;  // rows per warp-wide load: 2^5
 
+// Stored-matrix comparison path (csr.cu): count, scan, fill, multiply.
+size_t csr_smem_bytes(const LaunchArgs& a, int c64);
+int csr_prepare(size_t smem);
+int launch_csr_count(const LaunchArgs& a, int c64, size_t smem, int* counts, void* stream);
+int launch_csr_fill(const LaunchArgs& a, int c64, size_t smem, const long long* rp, int* col, void* val,
+                    void* stream);
+int csr_scan(const int* counts, long long* rp, long long dim, void* stream);
+int launch_csr_spmm(long long dim, int R, const long long* rp, const int* col, const void* val, const void* x,
+                    void* y, int c64, void* stream);
+
 // Host tridiagonal eigensolver + sums (tridiag.cpp); host_sums_sym: the
 // symmetric estimator of M_B from the matrices O_ij = <v_i|u.S|v_j>.
 ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,

@@ -51,11 +51,11 @@ def compare_tridiag(g, o, tol, steps=20):
 
 
 @pytest.mark.parametrize("case", ["ring6_s1", "mixed", "lattice4x3"])
-def test_ftlm_c128_matches_oracle(case, rng):
+def test_ftlm_c128_matches_oracle(case):
     if case == "ring6_s1":
         w, R, M = W.ring6_s1(), 10, 80
-    elif case == "mixed":
-        w, R, M = random_system(rng, [1, 2, 3, 2]), 5, 40
+    elif case == "mixed":  # its own generator: the system must not depend on the order tests run in
+        w, R, M = random_system(np.random.default_rng(2607), [1, 2, 3, 2]), 5, 40
     else:
         w, R, M = W.square_lattice(4, 3, seed=1), 6, 60
     s = F.System.from_dict(w)
@@ -63,9 +63,9 @@ def test_ftlm_c128_matches_oracle(case, rng):
     o = oracle.ftlm(osys(w), R=R, M=M, T=T, seed=5)
     compare_tridiag(g, o, 1e-10)
     cold = T >= 0.1
-    for k in KEYS:
-        assert rel(g[k], o[k], 1e-6, cold) < 1e-10, k
-        assert rel(g[k], o[k], 1e-6) < 1e-9, k
+    for k in KEYS:  # relative error with the module's floor for quantities passing through zero
+        assert rel(g[k], o[k], 1e-3, cold) < 1e-10, k
+        assert rel(g[k], o[k], 1e-3) < 1e-9, k
     assert abs(g["E0"] - o["E0"]) < 1e-10 * abs(o["E0"])
 
 
