@@ -248,7 +248,7 @@ typedef struct {
   int tile_rows;          /* rows per tile */
   int grid;               /* CTAs per H.v launch */
   int threads;            /* threads per CTA */
-  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..7) */
+  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..9) */
   /* symmetric runs (params.symmetric = 1); caller-allocated, may be NULL */
   double* M_B_sym;        /* [nT] sFTLM: -g sum_r <r|e^{-bH/2} u.S e^{-bH/2}|r> / sum_r <r|e^{-bH}|r>,
                              Eq. (E-2-G) with (E-2-H), shifted by E0 */
@@ -361,7 +361,10 @@ ftlm_status ftlm_sums_sym(int R, int M, const int* M_eff, const double* alpha, c
  *                 [5, n), so that every pair is a cube, mixed or lane-lane
  *                 pair of one launch (one output block per pass, summed
  *                 by the step); 6 / 7 = 3 / 5 with one 512-thread CTA per
- *                 SM instead of two of 256.  group_vectors is ignored and
+ *                 SM instead of two of 256; 8 / 9 = vector-major in two
+ *                 passes (cubes on bits [5, 5 + cube_bits) and on the top
+ *                 cube_bits bits; n_sites >= 5 + 2 cube_bits) with one
+ *                 512-thread / two 256-thread CTAs per SM.  group_vectors is ignored and
  *                 tile_cubes counts slabs of 2^(5 + cube_bits) rows per warp.
  *                 ftlm_apply_h on row-major blocks uses the row-major
  *                 register-cube kernel for these shapes.

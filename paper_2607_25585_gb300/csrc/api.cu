@@ -150,6 +150,7 @@ InstDesc base_desc(const ftlm_system* s, int c64) {
 struct HalfPlan {
   bool on = false;
   bool vm = false;  // vector-major kernel: R instances of one vector each (nvg = R, Rg = 1)
+  bool hybrid = false;  // vector-major two-pass form
   int real_pm = 0;
   int min_blocks = 2;
   int passes = 1;  // > 1: one launch per pass, cubes covering all bits
@@ -209,15 +210,17 @@ bool make_half(const ftlm_system* s, int R, int c64, int K, int Rg, int rows_fac
 // Vector-major spin-1/2 launch: K cube bits above the 5 lane bits, tiles of
 // 8 warps x rows_factor slabs of 2^(5+K) rows, R tiles ranges (one per vector).
 bool make_vm(const ftlm_system* s, int R, int c64, int K, int rows_factor, int min_blocks, bool multipass,
-             HalfPlan& h) {
+             HalfPlan& h, bool hybrid = false) {
   const HostSystem& hs = s->hs;
   if (!hs.all_half || K < 3 || K > 4 || hs.n < kVmLaneBits + K || rows_factor < 1) return false;
+  if (hybrid && hs.n < kVmLaneBits + 2 * K) return false;  // the two cubes must not overlap
   if (hs.dim >= (1ull << 31)) return false;  // 32-bit element indices
   h = HalfPlan();
   h.vm = true;
   h.K = K;
   h.Rg = 1;
-  h.passes = multipass ? (hs.n - kVmLaneBits + K - 1) / K : 1;  // cubes cover bits [5, n)
+  h.passes = hybrid ? 2 : (multipass ? (hs.n - kVmLaneBits + K - 1) / K : 1);  // cubes cover bits [5, n)
+  h.hybrid = hybrid;
   // 1: one 512-thread CTA per SM; 2 or 3: 256-thread CTAs (3 only in one pass)
   h.min_blocks = min_blocks == 1 ? 1 : (h.passes > 1 ? 2 : (min_blocks > 2 ? 3 : 2));
   h.real_pm = hs.real_pm ? 1 : 0;
@@ -298,7 +301,7 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   pl.half.on = false;
   if (sys.size() == 1 && pl.sh.half_K > 0 && pl.sh.half_vm && allow_vm &&
       make_vm(sys[0], R, c64, pl.sh.half_K, pl.sh.half_rows, pl.sh.half_min_blocks, pl.sh.half_multipass != 0,
-              pl.half)) {
+              pl.half, pl.sh.half_hybrid != 0)) {
     // the streaming modes see R one-vector instances of the same system
     const Shape keep = pl.sh;
     pl.sh = default_shape(1, c64);
@@ -349,9 +352,25 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.real_pm = pl.half.real_pm;
     a.min_blocks = pl.half.min_blocks;
     a.inline_one = (a.inline_one && pl.half.nvg == 1) ? 1 : 0;  // one vector: the descriptor by value
+    a.pass_stride = (long long)pl.half.nvg * pl.half.dim;
+    if (pl.half.hybrid) {  // two launches: the bottom cube (one-pass kernel), then the top cube adds its terms
+      LaunchArgs b = a;
+      b.single_pass = 1;
+      b.hybrid = 1;
+      b.npass = 1;
+      b.gather_alpha = 0;
+      b.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
+      const int e = launch_vm(b, pl.half.K, pl.half.min_blocks, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+      if (e) return e;
+      a.single_pass = 0;
+      a.hybrid = 2;
+      a.npass = 1;
+      a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
+      return launch_vm(a, pl.half.K, pl.half.min_blocks, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
+    }
     a.single_pass = pl.half.passes == 1 ? 1 : 0;
     a.npass = pl.half.passes;  // pass p writes y + p * R * d (vector-major blocks)
-    a.pass_stride = (long long)pl.half.nvg * pl.half.dim;
+    a.hybrid = 0;
     a.ntiles = pl.half.tiles_per_vg * pl.half.nvg * pl.half.passes;
     return launch_vm(a, pl.half.K, pl.half.min_blocks, pl.c64, pl.half.grid, pl.half.threads, pl.half.smem, st);
   }
@@ -513,7 +532,8 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
            pl.grid, p->breakdown_tol, u[0], u[1], u[2], p->obs_dir ? 1 : 0, p->stream);
   k += buf;
   k += p->symmetric ? "|sym" : "";
-  snprintf(buf, sizeof buf, "|half%d vm%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
+  snprintf(buf, sizeof buf, "|half%d vm%d hy%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
+           pl.half.hybrid ? 1 : 0,
            pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
   return k + buf;
 }
@@ -625,7 +645,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
       if (fused) {
         a.mode = kModeStep;
-        a.hq_parts = pl.half.vm ? pl.half.passes : 1;  // the passes' partial H q_j blocks
+        a.hq_parts = (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1;  // the passes' partial H q_j blocks
         a.hq_stride = (long long)R * (long long)sys[0]->hs.dim;
         CKI(launch_plan(pl, a, st));
         a.hq_parts = 1;
@@ -845,7 +865,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   ftlm_status ps = make_plan(sys, R, c64, pl, nullptr, true);
   if (ps != FTLM_OK) return ps;
   if (pl.half.on) {
-    ftlm_status hs_ = ensure_hq(sys[0], R, c64, pl.half.vm ? pl.half.passes : 1);
+    ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
   }
   if (p->symmetric) {  // the M Lanczos vectors of every vector
@@ -985,7 +1005,7 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
               sh.half_min_blocks = mb;
               if (s->hs.n >= K + 2) cands.push_back(sh);
             }
-    for (int mp : {0, 1})  // the vector-major gather (runs only)
+    for (int mp : {0, 1, 2})  // the vector-major gather (runs only): one pass, ceil((n-5)/K) passes, two passes
       for (int K : {3, 4})
         for (int f : {1, 2, 4, 8})
           for (int mb : {1, 2}) {  // one 512-thread or two 256-thread CTAs per SM
@@ -993,10 +1013,11 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
             sh.half_K = K;
             sh.Rg = largest_divisor_at_most(R, 16);
             sh.half_rows = f;
-            sh.half_multipass = mp;
+            sh.half_multipass = mp == 1 ? 1 : 0;
+            sh.half_hybrid = mp == 2 ? 1 : 0;
             sh.half_min_blocks = mb;
             sh.half_vm = 1;
-            if (s->hs.n >= kVmLaneBits + K) cands.push_back(sh);
+            if (s->hs.n >= kVmLaneBits + (mp == 2 ? 2 * K : K)) cands.push_back(sh);
           }
   } else {
     for (int thr : {128, 256})
@@ -1045,7 +1066,7 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (pl.half.vm && pl.half.passes > 1)  // the step then reads passes - 1 more H q blocks (~6 TB/s)
+    if (pl.half.vm && pl.half.passes > 1 && !pl.half.hybrid)  // the step then reads passes - 1 more H q blocks (~6 TB/s)
       ms += 5.0f * (float)((double)(pl.half.passes - 1) * (double)vbytes * R / 6.0e9);
     if (ms < best) {
       best = ms;
@@ -1384,7 +1405,9 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     if (!s->hs.all_half) return fail(FTLM_ERR_UNSUPPORTED, "register cubes need every site s = 1/2");
     if (cube_bits < 2 || cube_bits > 4 || s->hs.n < cube_bits + 2)
       return fail(FTLM_ERR_INVALID_ARG, "cube_bits must be 2..4 and at most n_sites - 2");
-    if (multipass < 0 || multipass > 7) return fail(FTLM_ERR_INVALID_ARG, "multipass must be in 0..7");
+    if (multipass < 0 || multipass > 9) return fail(FTLM_ERR_INVALID_ARG, "multipass must be in 0..9");
+    if (multipass >= 8 && (cube_bits < 3 || s->hs.n < kVmLaneBits + 2 * cube_bits))
+      return fail(FTLM_ERR_INVALID_ARG, "the two-pass form needs cube_bits 3..4 and n_sites >= 5 + 2 cube_bits");
     if (multipass >= 3 && (cube_bits < 3 || s->hs.n < kVmLaneBits + cube_bits))
       return fail(FTLM_ERR_INVALID_ARG, "the vector-major kernel needs cube_bits 3..4 and n_sites >= 5 + cube_bits");
     if (multipass < 3 && (group_vectors < 1 || group_vectors > nvec || group_vectors > 256))
@@ -1394,8 +1417,9 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     sh.Rg = multipass >= 3 ? largest_divisor_at_most(nvec, 16) : group_vectors;  // row-major fallback for apply_h
     sh.half_rows = tile_cubes;
     sh.half_multipass = (multipass == 1 || multipass == 5 || multipass == 7) ? 1 : 0;
-    // 2 and 4: 3-CTA register budget; 6 and 7: one 512-thread CTA per SM
-    sh.half_min_blocks = (multipass == 2 || multipass == 4) ? 3 : (multipass >= 6 ? 1 : 2);
+    sh.half_hybrid = multipass >= 8 ? 1 : 0;
+    // 2 and 4: 3-CTA register budget; 6, 7 and 8: one 512-thread CTA per SM
+    sh.half_min_blocks = (multipass == 2 || multipass == 4) ? 3 : ((multipass >= 6 && multipass <= 8) ? 1 : 2);
     sh.half_vm = multipass >= 3 ? 1 : 0;
   }
   std::lock_guard<std::mutex> lk(g_mu);

@@ -150,6 +150,7 @@ struct LaunchArgs {
   // writing its partial H x to y + p * pass_stride (complex elements)
   int npass = 1;
   long long pass_stride = 0;
+  int hybrid = 0;  // npass = 2: cubes on bits [5, 5 + K) and on the top K bits (see hv_vm.cu)
   // kModeStep / kModeEpilogue: H q_j = sum of hq_parts blocks hq + p * hq_stride
   int hq_parts = 1;
   long long hq_stride = 0;
@@ -166,6 +167,7 @@ struct Shape {
   int half_multipass = 0;  // spin-1/2 kernel: 1 = ceil(N/K) passes whose cubes cover all bits
   int half_min_blocks = 2; // spin-1/2 kernel: register budget of 2 or 3 CTAs per SM
   int half_vm = 0;         // spin-1/2 kernel: 1 = vector-major Lanczos block (ftlm_run only)
+  int half_hybrid = 0;     // vector-major: the two-pass form (cubes on bits [5, 5+K) and the top K bits)
   bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
 };
 

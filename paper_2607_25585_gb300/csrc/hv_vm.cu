@@ -108,6 +108,14 @@ size_t vm_smem_bytes(int n, int K, int threads, int npass, int c64) {
 // its own bits start at 5 + pK (the last cube may overlap the one before).
 __device__ __forceinline__ int vm_pass_lo(int p, int K, int n) { return min(kLaneBits + p * K, n - K); }
 
+// The two-pass form, two launches (a.hybrid): launch 1 is the one-pass kernel
+// (cube on bits [5, 5 + K)) doing everything except the terms of the top K
+// bits (a.hybrid = 1); launch 2 (a.hybrid = 2, multi-pass template) has its
+// cube on the top bits [n - K, n) and does their single flips, their pairs
+// with each other and their mixed pairs with the lane bits and the middle bits
+// [5 + K, n - K), adds the first launch's sums and writes the complete H x.
+// Pairs of a bottom-cube bit with a top bit are mixed pairs of launch 1.
+
 // MP: the multi-pass form, all a.npass passes in this launch.  Pass p's cube
 // spans bits [s0, s0 + K), s0 = min(5 + pK, n - K); its cube bits >= 5 + pK
 // are its own: their single flips, their pairs with each other and their
@@ -145,8 +153,12 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
   const real* t = reinterpret_cast<const real*>(d.tab);  // every instance of the launch shares the system
   const TabLayout& L = d.lay;
   const int bd = blockDim.x;
+  const bool top = MP && a.hybrid == 2;       // the top-cube launch of the two-pass form
+  const bool bottom = !MP && a.hybrid == 1;   // the bottom-cube launch of the two-pass form
+  // cube of pass p: bits [cube_lo(p), cube_lo(p) + K)
+  auto cube_lo = [&](int p) { return top ? n - K : vm_pass_lo(p, K, n); };
   // the last pass's cube bits below its own bits (overlap with the pass before)
-  const int ov_lo = vm_pass_lo(P - 1, K, n), ov_hi = MP ? CB + (P - 1) * K : ov_lo;
+  const int ov_lo = vm_pass_lo(P - 1, K, n), ov_hi = (MP && !top) ? CB + (P - 1) * K : ov_lo;
   auto overlap = [&](int i) { return i >= ov_lo && i < ov_hi; };
 
   // ---- per-system tables ----
@@ -178,7 +190,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
   }
   for (int q = threadIdx.x; q < P * n * NR; q += bd) {  // cube part of F_j, per pass
     const int pp = q / (n * NR), j = (q / NR) % n, r = q % NR;
-    const int c0 = vm_pass_lo(pp, K, n);
+    const int c0 = MP ? cube_lo(pp) : CB;
     real fr = 0, fi = 0;
     if (!(pp == P - 1 && overlap(j))) {
       for (int c = 0; c < K; ++c) {
@@ -259,14 +271,22 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       y0 = insts[inst].y;
       cur = inst;
     }
-    const int s0 = MP ? vm_pass_lo(pass, K, n) : CB;         // cube bits [s0, s0 + K)
-    const int cnew = MP ? CB + pass * K - s0 : 0;            // first own cube bit (cube-relative)
-    const bool first = !MP || pass == 0;
+    const int s0 = MP ? cube_lo(pass) : CB;                 // cube bits [s0, s0 + K)
+    const int cnew = (MP && !top) ? CB + pass * K - s0 : 0;  // first own cube bit (cube-relative)
+    const bool first = !MP || (pass == 0 && !top);
+    // neighbour bits: the lane bits and [nb_lo, nb_hi) (the bits above the cube,
+    // or for the top cube of the two-pass form the middle bits below it)
+    const int nb_lo = top ? CB + K : s0 + K;
+    const int nb_hi = top ? s0 : n;
+    // single flips of neighbour bits below single_hi and pairs of two neighbour
+    // bits below pair_hi belong to this pass (only in the first pass)
+    const int single_hi = !MP ? (bottom ? n - K : n) : CB;
+    const int pair_hi = single_hi;
     const real* cpb = (MP && pass == P - 1) ? S.cpl : S.cp;  // overlap pairs zeroed in the last pass
     const real* fcp = S.fc + (size_t)pass * n * NR * 2;
     v2* const y = reinterpret_cast<v2*>(y0) + (MP ? pass * a.pass_stride : 0);
     const unsigned long long lowmask = (1ull << (s0 - CB)) - 1ull;  // outer bits between the lanes and the cube
-    const int nnb = CB + n - s0 - K;  // neighbour bits: the lane bits and the bits above the cube
+    const int nnb = CB + nb_hi - nb_lo;
     auto in_cube = [&](int i) { return i >= s0 && i < s0 + K; };
     const long long unit0 = (long long)ptile * units_per_tile;
     for (int ui = warp; ui < units_per_tile; ui += nwarps) {
@@ -316,6 +336,17 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       }
       __syncwarp();
       const long long row0 = (long long)(base | (unsigned long long)lane);
+      if (MP && ui + nwarps < units_per_tile && (long long)u + nwarps < nunits) {
+        // the warp's next unit: its rows of x (and of y for the top launch) to L2 now,
+        // so that the unit's first loads do not wait on HBM
+        const unsigned long long un = u + (unsigned long long)nwarps;
+        const unsigned long long bn = ((un >> (s0 - CB)) << (s0 + K)) | ((un & lowmask) << CB) | (unsigned long long)lane;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const v2*>(x) + ((unsigned)bn + ((unsigned)r << s0))));
+          if (top) asm volatile("prefetch.global.L2 [%0];" ::"l"(y + ((unsigned)bn + ((unsigned)r << s0))));
+        }
+      }
       v2 xo[NR];
       Cx<real> acc[NR];
 #pragma unroll
@@ -366,13 +397,13 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       // cube serves the mixed pairs (c, j) and, where this pass owns it, the
       // single flip of j
       for (int jj = 0; jj < nnb; ++jj) {
-        const int j = jj < CB ? jj : s0 + K + (jj - CB);
+        const int j = jj < CB ? jj : nb_lo + (jj - CB);
         const int bj = (int)((row0 >> j) & 1);
         const long long nb = row0 ^ (1ll << j);
         v2 yv[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) yv[r] = ldx_cube<real, MP>(x, nb, r, s0);
-        if (!MP || (first && j < CB)) {
+        if (first && j < single_hi) {
           const real br = fs[2 * j] + S.fl[2 * (j * 32 + lane)], bi = fs[2 * j + 1] + S.fl[2 * (j * 32 + lane) + 1];
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
@@ -380,7 +411,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
             acc[r].mac(br + fcp[2 * (j * NR + r)], bj ? fim : -fim, yv[r]);
           }
         }
-        const bool uniform = j >= CB;  // bit j (above the cube) is the same for the whole warp
+        const bool uniform = j >= CB;  // bit j (not a lane bit) is the same for the whole warp
 #pragma unroll
         for (int c = 0; c < K; ++c) {
           const int sc = s0 + c;
@@ -390,7 +421,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
               const int bc = (r >> c) & 1;
-              const int idx = 2 * bc + bj;  // j > sc here
+              const int idx = j < sc ? 2 * bj + bc : 2 * bc + bj;
               if (bc != bj) acc[r].mac_re(cp[2 * idx], yv[r ^ (1 << c)]);
               else acc[r].mac(cp[2 * idx], cp[2 * idx + 1], yv[r ^ (1 << c)]);
             }
@@ -404,16 +435,17 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
           }
         }
       }
-      // pairs of two neighbour bits: one coefficient for the whole cube (without
-      // MP every such pair; with MP only the lane-lane pairs, in pass 0)
+      // pairs of two neighbour bits below pair_hi: one coefficient for the whole
+      // cube (in one pass every such pair; in the multi-pass form only the
+      // lane-lane pairs, in the two-pass form those of the lane and middle bits)
       if (first) {
-        const int npb = MP ? CB : nnb;
+        const int npb = CB + max(0, min(nb_hi, pair_hi) - nb_lo);
         for (int jj = 1; jj < npb; ++jj) {
-          const int j = jj < CB ? jj : s0 + K + (jj - CB);
+          const int j = jj < CB ? jj : nb_lo + (jj - CB);
           const int bj = (int)((row0 >> j) & 1);
 #pragma unroll 2
           for (int ii = 0; ii < jj; ++ii) {
-            const int i = ii < CB ? ii : s0 + K + (ii - CB);
+            const int i = ii < CB ? ii : nb_lo + (ii - CB);
             const int bi = (int)((row0 >> i) & 1);
             const real* cp = cpb + tri(i, j) * 8 + 2 * (2 * bi + bj);
             const real cr = cp[0], ci = cp[1];
@@ -430,6 +462,13 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
             }
           }
         }
+      }
+      if (top) {  // add the bottom launch's sums: all loads first
+        v2 prev[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) prev[r] = __ldcs(y + ((unsigned)row0 + ((unsigned)r << s0)));
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r].add(prev[r]);
       }
       real pd = 0;
 #pragma unroll
@@ -494,7 +533,12 @@ __global__ void __launch_bounds__(256) vm_stream_kernel(const __grid_constant__ 
     const int inst = tile / a.tiles_per_vg;
     if (inst != cur) {
       if (cur >= 0) flush(cur);
-      if (threadIdx.x == 0) d = a.inst[inst];
+      {  // the instance's descriptor, copied by the whole CTA in 8-byte words
+        static_assert(sizeof(InstDesc) % 8 == 0, "InstDesc is copied in 8-byte words");
+        const long long* src = reinterpret_cast<const long long*>(a.inst + inst);
+        long long* dst = reinterpret_cast<long long*>(&d);
+        for (int w = threadIdx.x; w < (int)(sizeof(InstDesc) / 8); w += bd) dst[w] = __ldg(src + w);
+      }
       __syncthreads();
       const int j = a.step;
       real sg = 0, bs = 0, cf = 0;

@@ -188,11 +188,12 @@ def test_ftlm_every_kernel_variant(shape):
 
 
 @pytest.mark.parametrize("shape", [(3, 1, 1, 3), (4, 1, 2, 3), (3, 1, 4, 4), (4, 1, 1, 4), (3, 1, 1, 5), (4, 1, 2, 5),
-                                   (4, 1, 1, 6), (3, 1, 2, 7)])
+                                   (4, 1, 1, 6), (3, 1, 2, 7), (3, 1, 1, 8), (3, 1, 2, 9)])
 def test_ftlm_vector_major_matches_oracle(shape, rng):
     """Vector-major Lanczos block (each vector contiguous; a warp owns 32
-    consecutive rows, a thread a cube above them), in one pass or in passes
-    whose cubes cover bits [5, n) (the last cube overlapping the one before):
+    consecutive rows, a thread a cube above them), in one pass, in passes
+    whose cubes cover bits [5, n) (the last cube overlapping the one before),
+    or in two passes (cubes on bits [5, 5+K) and on the top K bits):
     random start with a vector offset, basis start and a user block
     (transposed on the device) against the oracle step by step (complex128)
     and in the thermodynamics (complex64), on 4x3 and 4x4 lattices."""
@@ -236,10 +237,10 @@ def test_full_size_lanczos_sample():
         g = F.run(s, R=1, M=M, T=T, seed=2, dtype=dt)
         compare_tridiag(g, o, tol)
         try:  # the vector-major block, one pass and four
-            for mp in (3, 5):
+            for mp in (3, 5, 8):
                 F.tune_shape(s, 1, dt, 4, 1, 1, mp)
                 g = F.run(s, R=1, M=M, T=T, seed=2, dtype=dt)
-                assert g["shape"]["vector_major"] == 1 and g["shape"]["passes"] == (1 if mp == 3 else 4)
+                assert g["shape"]["vector_major"] == 1 and g["shape"]["passes"] == {3: 1, 5: 4, 8: 2}[mp]
                 compare_tridiag(g, o, tol)
         finally:
             F.tune_shape(s, 1, dt, -1)
