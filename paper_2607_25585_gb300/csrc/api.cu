@@ -168,6 +168,7 @@ struct Plan {
   LaunchArgs base;
   std::vector<int> tile_start;
   HalfPlan half;  // spin-1/2 kernel for the H.v modes, when applicable
+  int wideV = 0;  // general kernel: H.v with 4 or 8 complex64 vectors per thread (0 = off)
 };
 
 int largest_divisor_at_most(int R, int cap) {
@@ -278,6 +279,14 @@ ftlm_status make_general(const std::vector<ftlm_system*>& sys, int R, int c64, P
   const int sms = std::max(1, device_sm_count());
   pl.grid = std::max(1, std::min(a.ntiles, sms * per_sm));
   pl.base = a;
+  // H.v with more vectors per thread: the matrix elements of a row are computed
+  // once for 4 or 8 vectors instead of 2 (complex64; the same tiles)
+  pl.wideV = 0;
+  if (c64 && R >= 4 && R % 4 == 0) {
+    const int Vw = R % 8 == 0 ? 8 : 4, Cw = R / Vw;
+    // (H.v keeps no reduction space in shared memory, so pl.smem covers it)
+    if (pl.sh.threads % Cw == 0 && pl.sh.rows_per_tile % (pl.sh.threads / Cw) == 0) pl.wideV = Vw;
+  }
   return FTLM_OK;
 }
 
@@ -400,6 +409,10 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
       if (e) return e;
     }
     return 0;
+  }
+  if (pl.wideV && a.mode == kModeApply) {
+    a.C = a.R / pl.wideV;
+    return launch_rows_wide(a, pl.wideV, pl.grid, pl.sh.threads, pl.smem, st);
   }
   // the streaming modes need far fewer CTAs than the gathers to saturate HBM,
   // and fewer CTAs means fewer partial sums for the last CTA to add up
@@ -585,10 +598,11 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   const InstDesc* d_start = d_even + 2 * nd;
   const InstDesc* d_gather_even = d_even + 3 * nd;  // split steps: x = q_j, y = Hq
   const InstDesc* d_gather_odd = d_even + 4 * nd;
-  const bool split = pl.half.on;  // the spin-1/2 gather runs alone; the step epilogue streams afterwards
+  // the spin-1/2 gathers and the wide general gather run alone; the step epilogue streams afterwards
+  const bool split = pl.half.on || pl.wideV;
   // single-pass gathers also sum Re<q_j|H q_j>, so alpha_j is known before the
   // epilogue, which then finishes the step in one pass (no separate update)
-  const bool fused = split && (pl.half.passes == 1 || pl.half.vm);
+  const bool fused = pl.half.on && (pl.half.passes == 1 || pl.half.vm);
   LaunchArgs a = pl.base;
   a.tile_start = reinterpret_cast<const int*>(ctx.tiles.p);
   a.partials = reinterpret_cast<double*>(ctx.partials.p);
@@ -867,6 +881,11 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   if (pl.half.on) {
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
+  } else if (pl.wideV) {
+    for (auto* s : sys) {
+      ftlm_status hs_ = ensure_hq(s, R, c64, 1);
+      if (hs_ != FTLM_OK) return hs_;
+    }
   }
   if (p->symmetric) {  // the M Lanczos vectors of every vector
     ftlm_system* s0 = sys[0];

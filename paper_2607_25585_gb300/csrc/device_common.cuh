@@ -29,6 +29,36 @@ struct VecIO<float, 2> {
   }
 };
 
+// V = 4, 8: complex64 values of V consecutive vectors, 16-byte loads
+template <int V>
+struct VecIOWide {
+  static __device__ __forceinline__ void ldg(const void* b, long long idx, float* re, float* im) {
+    const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(b) + idx);
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) {
+      const float4 t = __ldg(p + h);
+      re[2 * h] = t.x; im[2 * h] = t.y; re[2 * h + 1] = t.z; im[2 * h + 1] = t.w;
+    }
+  }
+  static __device__ __forceinline__ void ld(const void* b, long long idx, float* re, float* im) {
+    const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(b) + idx);
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) {
+      const float4 t = p[h];
+      re[2 * h] = t.x; im[2 * h] = t.y; re[2 * h + 1] = t.z; im[2 * h + 1] = t.w;
+    }
+  }
+  static __device__ __forceinline__ void st(void* b, long long idx, const float* re, const float* im) {
+    float4* p = reinterpret_cast<float4*>(reinterpret_cast<float2*>(b) + idx);
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) p[h] = make_float4(re[2 * h], im[2 * h], re[2 * h + 1], im[2 * h + 1]);
+  }
+};
+template <>
+struct VecIO<float, 4> : VecIOWide<4> {};
+template <>
+struct VecIO<float, 8> : VecIOWide<8> {};
+
 template <>
 struct VecIO<float, 1> {
   static __device__ __forceinline__ void ldg(const void* b, long long idx, float* re, float* im) {

@@ -188,7 +188,8 @@ int launch_time_reverse(const InstDesc* h, const void* x, void* y, int R, int c6
 int launch_sdir_vm(const InstDesc* h, const void* V, void* W, int nv, long long c0, int cnt, int T, int c64,
                    void* stream);
 int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
-size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads);
+size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads, int Vmax = 0);
+int launch_rows_wide(const LaunchArgs& a, int V, int grid, int threads, size_t smem, void* stream);
 int prepare_rows_kernels(size_t smem);
 int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int mode);
 int device_sm_count();

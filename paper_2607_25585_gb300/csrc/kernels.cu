@@ -110,11 +110,11 @@ __device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst,
 template <typename real, int V, int MODE>
 __global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SmemView s = carve<real>(smem_raw, a, V);
-  __shared__ InstDesc d;
-  __shared__ int is_last;
   constexpr bool kPartials = MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate ||
                              MODE == kModeStartNorm || MODE == kModeStep;
+  const SmemView s = carve<real>(smem_raw, a, kPartials ? V : 0);  // no reduction space without partial sums
+  __shared__ InstDesc d;
+  __shared__ int is_last;
   const InstDesc* insts = a.inline_one ? &a.one : a.inst;
   constexpr int NP = V * kNumPartials;
   double acc[NP];
@@ -476,8 +476,8 @@ __global__ void sdir_vm_kernel(InstDesc d, const real* __restrict__ V, real* __r
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads) {
-  const int V = c64 ? 2 : 1;
+size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads, int Vmax) {
+  const int V = Vmax > 0 ? Vmax : (c64 ? 2 : 1);
   const size_t realsz = c64 ? 4 : 8;
   size_t off = ((size_t)a.tab_reals * realsz + 15) & ~size_t(15);
   off += (size_t)a.max_n * 8;
@@ -512,7 +512,22 @@ int prepare_rows_kernels(size_t smem) {
   int e = allow_smem<float, 2>((int)smem);
   if (!e) e = allow_smem<float, 1>((int)smem);
   if (!e) e = allow_smem<double, 1>((int)smem);
+  const void* wide[] = {(const void*)rows_kernel<float, 4, kModeApply>, (const void*)rows_kernel<float, 8, kModeApply>};
+  for (const void* k : wide)
+    if (!e) e = (int)cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
+}
+
+// H.v with V = 4 or 8 complex64 vectors per thread (a.C = R / V): the row's
+// matrix elements are computed once for V vectors (16 per thread, one thread
+// per row at R = 16, was twice as slow: the loads no longer coalesce).
+int launch_rows_wide(const LaunchArgs& a, int V, int grid, int threads, size_t smem, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (a.mode != kModeApply || a.R % V != 0 || a.C != a.R / V) return (int)cudaErrorInvalidValue;
+  if (V == 8) rows_kernel<float, 8, kModeApply><<<grid, threads, smem, st>>>(a);
+  else if (V == 4) rows_kernel<float, 4, kModeApply><<<grid, threads, smem, st>>>(a);
+  else return (int)cudaErrorInvalidValue;
+  return (int)cudaGetLastError();
 }
 
 template <typename real, int V>

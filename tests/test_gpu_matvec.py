@@ -36,7 +36,7 @@ def built():
 
 @pytest.mark.parametrize("name", sorted(SYSTEMS))
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("R", [1, 3, 10, 64])
+@pytest.mark.parametrize("R", [1, 3, 4, 8, 10, 64])
 def test_apply_h_matches_oracle(name, dtype, R, rng):
     w = SYSTEMS[name](rng)
     s = F.System.from_dict(w)
