@@ -65,3 +65,45 @@ def test_two_ranks_reproduce_one_process():
         for k in ("lnZ", "E", "C", "M_B"):
             ref = full[k]
             assert np.max(np.abs(merged[k] - ref) / np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())) < 1e-11, k
+
+
+def _worker_sym(rank, world, port, out_path):
+    """Symmetric FTLM sharded the same way: each rank gathers its vectors'
+    alpha, beta, M_eff and O_ij = <v_i|u.S|v_j>; rank 0 merges with the
+    host-only ftlm_sums_sym (common E0 over all vectors)."""
+    import torch.distributed as dist
+
+    import oracle
+    import paper_2607_25585_gb300 as F
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = W.ring(N=5, two_s=2)
+    s = oracle.System(**{k: v for k, v in w.items() if k != "name"})
+    T = W.temperatures()
+    o = oracle.sftlm(s, R=R_LOCAL, M=M, T=T, seed=4, vec_offset=rank * R_LOCAL, start="pairs")
+    parts = [None] * world
+    dist.all_gather_object(parts, {k: o[k] for k in ("alpha", "beta", "O", "M_eff")})
+    if rank == 0:
+        cat = {k: np.concatenate([p[k] for p in parts]) for k in ("alpha", "beta", "O", "M_eff")}
+        mb, _ = F.sums_sym(cat["alpha"], cat["beta"], cat["O"], cat["M_eff"], s.g, T)
+        np.savez(out_path, M_B_sym=mb)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_symmetric_estimator():
+    import oracle
+    import paper_2607_25585_gb300 as F
+
+    oracle.build()
+    F.build()
+    world = 2
+    with tempfile.TemporaryDirectory() as td:
+        out = os.path.join(td, "merged_sym.npz")
+        mp.spawn(_worker_sym, args=(world, _free_port(), out), nprocs=world, join=True)
+        merged = np.load(out)["M_B_sym"]
+        w = W.ring(N=5, two_s=2)
+        s = oracle.System(**{k: v for k, v in w.items() if k != "name"})
+        full = oracle.sftlm(s, R=world * R_LOCAL, M=M, T=W.temperatures(), seed=4, start="pairs")["M_B_sym"]
+        assert np.max(np.abs(merged - full) / np.maximum(np.abs(full), 1e-6 * np.abs(full).max())) < 1e-11
