@@ -81,8 +81,15 @@ __device__ VmSmem<real> vm_carve(unsigned char* raw, int n, int K, int npass, in
   s.ec = p;
   p += NR;
   s.ws = p;
-  warp_stride = 2 * n + kLaneBits + K + 1;
+  warp_stride = (2 * n + kLaneBits + K + 1 + 1) & ~1;  // even: each warp's fs starts at a pair boundary
   return s;
+}
+
+// a (re, im) pair of a shared-memory table as one 8- or 16-byte access (the
+// tables keep every pair at an even offset from a 16-byte-aligned base)
+template <typename real>
+__device__ __forceinline__ typename Cx<real>::v2 ld2(const real* p) {
+  return *reinterpret_cast<const typename Cx<real>::v2*>(p);
 }
 
 // zz coefficient of sites (i, j), stored for i < j
@@ -100,7 +107,7 @@ size_t vm_smem_bytes(int n, int K, int threads, int npass, int c64) {
   const int NR = 1 << K, nwarps = threads / 32;
   const size_t reals = (size_t)(n * (n - 1) / 2) * 8 * (npass > 1 ? 2 : 1) + (size_t)n * 32 * 2 +
                        (size_t)npass * n * NR * 2 + 32 + (size_t)K * 32 + NR +
-                       (size_t)nwarps * (2 * n + kLaneBits + K + 1);
+                       (size_t)nwarps * ((2 * n + kLaneBits + K + 2) & ~1);
   return reals * (c64 ? 4 : 8);
 }
 
@@ -375,12 +382,14 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       for (int c = 0; c < K; ++c) {
         const int sc = s0 + c;
         const real om = (MP && c < cnew) ? (real)0 : (real)1;
-        const real br = om * (fs[2 * sc] + S.fl[2 * (sc * 32 + lane)]);
-        const real bi = om * (fs[2 * sc + 1] + S.fl[2 * (sc * 32 + lane) + 1]);
+        const v2 f0 = ld2(fs + 2 * sc), f1 = ld2(S.fl + 2 * (sc * 32 + lane));
+        const real br = om * (f0.x + f1.x);
+        const real bi = om * (f0.y + f1.y);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          const real fr = br + fcp[2 * (sc * NR + r)];
-          const real fim = bi + fcp[2 * (sc * NR + r) + 1];
+          const v2 fc = ld2(fcp + 2 * (sc * NR + r));
+          const real fr = br + fc.x;
+          const real fim = bi + fc.y;
           acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
         }
 #pragma unroll
@@ -389,7 +398,8 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             const int idx = 2 * ((r >> c1) & 1) + ((r >> c) & 1);
-            acc[r].mac(cp[2 * idx], cp[2 * idx + 1], xo[r ^ (1 << c) ^ (1 << c1)]);
+            const v2 cv = ld2(cp + 2 * idx);
+            acc[r].mac(cv.x, cv.y, xo[r ^ (1 << c) ^ (1 << c1)]);
           }
         }
       }
@@ -404,33 +414,44 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
 #pragma unroll
         for (int r = 0; r < NR; ++r) yv[r] = ldx_cube<real, MP>(x, nb, r, s0);
         if (first && j < single_hi) {
-          const real br = fs[2 * j] + S.fl[2 * (j * 32 + lane)], bi = fs[2 * j + 1] + S.fl[2 * (j * 32 + lane) + 1];
+          const v2 f0 = ld2(fs + 2 * j), f1 = ld2(S.fl + 2 * (j * 32 + lane));
+          const real br = f0.x + f1.x, bi = f0.y + f1.y;
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            const real fim = bi + fcp[2 * (j * NR + r) + 1];
-            acc[r].mac(br + fcp[2 * (j * NR + r)], bj ? fim : -fim, yv[r]);
+            const v2 fc = ld2(fcp + 2 * (j * NR + r));
+            const real fim = bi + fc.y;
+            acc[r].mac(br + fc.x, bj ? fim : -fim, yv[r]);
           }
         }
         const bool uniform = j >= CB;  // bit j (not a lane bit) is the same for the whole warp
 #pragma unroll
         for (int c = 0; c < K; ++c) {
           const int sc = s0 + c;
-          // pair (min, max) and the row's bits in that order
-          const real* cp = cpb + (j < sc ? tri(j, sc) : tri(sc, j)) * 8;
-          if (uniform && real_fast_pm) {
+          const bool lo = j < sc;
+          // pair (min, max); its coefficients for the row's bit c = 0 and = 1 (bit j is bj)
+          const real* cp = cpb + (lo ? tri(j, sc) : tri(sc, j)) * 8;
+          const int i0 = lo ? 2 * bj : bj, i1 = lo ? 2 * bj + 1 : 2 + bj;
+          const v2 cv0 = ld2(cp + 2 * i0), cv1 = ld2(cp + 2 * i1);
+          const real c0r = cv0.x, c0i = cv0.y, c1r = cv1.x, c1i = cv1.y;
+          if (uniform && real_fast_pm) {  // rows whose bit c differs from bj: the real s+ s- coefficient
+            if (bj) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-              const int bc = (r >> c) & 1;
-              const int idx = j < sc ? 2 * bj + bc : 2 * bc + bj;
-              if (bc != bj) acc[r].mac_re(cp[2 * idx], yv[r ^ (1 << c)]);
-              else acc[r].mac(cp[2 * idx], cp[2 * idx + 1], yv[r ^ (1 << c)]);
+              for (int r = 0; r < NR; ++r) {
+                if ((r >> c) & 1) acc[r].mac(c1r, c1i, yv[r ^ (1 << c)]);
+                else acc[r].mac_re(c0r, yv[r ^ (1 << c)]);
+              }
+            } else {
+#pragma unroll
+              for (int r = 0; r < NR; ++r) {
+                if ((r >> c) & 1) acc[r].mac_re(c1r, yv[r ^ (1 << c)]);
+                else acc[r].mac(c0r, c0i, yv[r ^ (1 << c)]);
+              }
             }
           } else {
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-              const int bc = (r >> c) & 1;
-              const int idx = j < sc ? 2 * bj + bc : 2 * bc + bj;
-              acc[r].mac(cp[2 * idx], cp[2 * idx + 1], yv[r ^ (1 << c)]);
+              if ((r >> c) & 1) acc[r].mac(c1r, c1i, yv[r ^ (1 << c)]);
+              else acc[r].mac(c0r, c0i, yv[r ^ (1 << c)]);
             }
           }
         }
@@ -448,7 +469,8 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
             const int i = ii < CB ? ii : nb_lo + (ii - CB);
             const int bi = (int)((row0 >> i) & 1);
             const real* cp = cpb + tri(i, j) * 8 + 2 * (2 * bi + bj);
-            const real cr = cp[0], ci = cp[1];
+            const v2 cv = ld2(cp);
+            const real cr = cv.x, ci = cv.y;
             const long long nb = row0 ^ (1ll << i) ^ (1ll << j);
             v2 yv[NR];
 #pragma unroll
