@@ -275,10 +275,6 @@ ftlm_status make_general(const std::vector<ftlm_system*>& sys, int R, int c64, P
   if (pl.smem > 227 * 1024) return fail(FTLM_ERR_UNSUPPORTED, "coupling tables do not fit in shared memory");
   ftlm_status ps = prepare_smem(std::max<size_t>(pl.smem, 48 * 1024));
   if (ps != FTLM_OK) return ps;
-  const int per_sm = pl.sh.ctas_per_sm > 0 ? pl.sh.ctas_per_sm : rows_max_ctas_per_sm(c64, pl.sh.threads, pl.smem, 0);
-  const int sms = std::max(1, device_sm_count());
-  pl.grid = std::max(1, std::min(a.ntiles, sms * per_sm));
-  pl.base = a;
   // H.v with more vectors per thread: the matrix elements of a row are computed
   // once for 4 or 8 vectors instead of 2 (complex64; the same tiles)
   pl.wideV = 0;
@@ -287,6 +283,20 @@ ftlm_status make_general(const std::vector<ftlm_system*>& sys, int R, int c64, P
     // (H.v keeps no reduction space in shared memory, so pl.smem covers it)
     if (pl.sh.threads % Cw == 0 && pl.sh.rows_per_tile % (pl.sh.threads / Cw) == 0) pl.wideV = Vw;
   }
+  // the grid fills the SMs with the kernel that carries H.v.  The wide H.v
+  // kernel runs two CTAs per SM while a system's block fits in the L2
+  // (its gathers are served on chip and more L1 per tile pays), and as many as
+  // fit once the block spills to HBM (the gathers' latency wants the warps).
+  int per_sm = pl.sh.ctas_per_sm > 0 ? pl.sh.ctas_per_sm : rows_max_ctas_per_sm(c64, pl.sh.threads, pl.smem, pl.wideV);
+  if (pl.sh.ctas_per_sm <= 0 && pl.wideV) {
+    long long maxdim = 0;
+    for (auto* s : sys) maxdim = std::max(maxdim, (long long)s->hs.dim);
+    const long long block_bytes = maxdim * R * 8;
+    if (block_bytes <= device_l2_bytes()) per_sm = std::min(per_sm, 2);
+  }
+  const int sms = std::max(1, device_sm_count());
+  pl.grid = std::max(1, std::min(a.ntiles, sms * per_sm));
+  pl.base = a;
   return FTLM_OK;
 }
 

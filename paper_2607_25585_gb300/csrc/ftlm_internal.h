@@ -33,6 +33,9 @@ struct TabLayout {
   int off_bz = 0;       // [n][2]     single-ion d e_z b: multiplies (s^z s+ + s+ s^z)
   int off_bb = 0;       // [n][2]     single-ion d b^2: multiplies s+ s+
   int off_hz = 0;       // [n]        coefficient of s^z_i from the Zeeman term
+  // packed copies for the general row kernel (one 16-byte shared-memory access each)
+  int off_site4 = 0;    // [n][qmax][4]  (<a|s+|a-1>, <a|s-|a+1>, m, single-ion diagonal)
+  int off_pair4 = 0;    // [n][n][4]     (s+_i s-_j re, im, s+_i s+_j re, im), i < j
   int total = 0;
 };
 
@@ -191,8 +194,10 @@ int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
 size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads, int Vmax = 0);
 int launch_rows_wide(const LaunchArgs& a, int V, int grid, int threads, size_t smem, void* stream);
 int prepare_rows_kernels(size_t smem);
-int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int mode);
+// CTAs per SM of the Lanczos-mode row kernel, or of the wide H.v kernel when wideV is 4 or 8
+int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int wideV);
 int device_sm_count();
+long long device_l2_bytes();
 
 // Spin-1/2 register-cube kernel (hv_half.cu): modes kModeApply and kModeLanczos
 // of a single instance with every site s = 1/2.

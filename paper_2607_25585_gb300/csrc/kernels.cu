@@ -108,7 +108,8 @@ __device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst,
 // the tile loop shared by every mode
 // ---------------------------------------------------------------------------
 template <typename real, int V, int MODE>
-__global__ void __launch_bounds__(256) rows_kernel(const __grid_constant__ LaunchArgs a) {
+// complex64: three 256-thread CTAs per SM (at most 85 registers a thread)
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(const __grid_constant__ LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kPartials = MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate ||
                              MODE == kModeStartNorm || MODE == kModeStep;
@@ -483,6 +484,7 @@ size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads, int Vmax) {
   off += (size_t)a.max_n * 8;
   off += ((size_t)a.max_n * 4 + 15) & ~size_t(15);
   off += (size_t)threads * kNumPartials * V * 8;
+  off += ((size_t)a.max_n * threads * realsz + 15) & ~size_t(15);  // the per-thread m columns
   off += (size_t)a.max_n * threads;
   return off;
 }
@@ -554,11 +556,13 @@ int launch_rows(const LaunchArgs& a, int c64, int grid, int threads, size_t smem
   return launch_mode<double, 1>(a, grid, threads, smem, st);
 }
 
-int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int mode) {
+int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int wideV) {
   int n = 0;
   cudaError_t e;
-  (void)mode;  // the caller has raised the shared-memory limit to >= smem
-  if (c64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<float, 2, kModeLanczos>, threads, smem);
+  // the caller has raised the shared-memory limit to >= smem
+  if (wideV == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<float, 8, kModeApply>, threads, smem);
+  else if (wideV == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<float, 4, kModeApply>, threads, smem);
+  else if (c64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<float, 2, kModeLanczos>, threads, smem);
   else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_kernel<double, 1, kModeLanczos>, threads, smem);
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
@@ -684,6 +688,16 @@ int device_sm_count() {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
+}
+
+long long device_l2_bytes() {
+  static long long cached[64] = {};
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return 0;
   if (dev >= 0 && dev < 64) cached[dev] = n;
   return n;
 }

@@ -44,6 +44,8 @@ TabLayout make_layout(int n, int qmax) {
   L.off_bz = take(2 * n);
   L.off_bb = take(2 * n);
   L.off_hz = take(n);
+  L.off_site4 = take(4 * n * qmax);
+  L.off_pair4 = take(4 * n * n);
   L.total = o;
   return L;
 }
@@ -222,6 +224,22 @@ ftlm_status build_host_system(int n, const int* two_s, const double* J, const do
       if (t[L.off_pm + 2 * ij + 1] != 0.0) real_pm = false;
     }
   hs.real_pm = real_pm;
+  // the packed copies
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < qmax; ++a) {
+      double* q4 = &t[L.off_site4 + 4 * (i * qmax + a)];
+      q4[0] = t[L.off_up1 + i * qmax + a];
+      q4[1] = t[L.off_dn1 + i * qmax + a];
+      q4[2] = t[L.off_m + i * qmax + a];
+      q4[3] = t[L.off_iondiag + i * qmax + a];
+    }
+  for (int ij = 0; ij < n * n; ++ij) {
+    double* p4 = &t[L.off_pair4 + 4 * ij];
+    p4[0] = t[L.off_pm + 2 * ij];
+    p4[1] = t[L.off_pm + 2 * ij + 1];
+    p4[2] = t[L.off_pp + 2 * ij];
+    p4[3] = t[L.off_pp + 2 * ij + 1];
+  }
   return FTLM_OK;
 }
 
