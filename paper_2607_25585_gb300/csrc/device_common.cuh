@@ -115,6 +115,78 @@ __device__ __forceinline__ void gather_mac(const void* x, long long nu, int R, i
 //   Epilogue: sig = sigma_j, bsp = beta_{j-1} sigma_{j-1};
 //   Step: the same and coef = alpha_j sigma_j;  Update: coef = alpha_j sigma_j;
 //   Scale: coef = the factor.
+// One element group of the recurrence step (kModeStep):
+//   w = sigma H q_j - beta_j sigma_{j-1} q_{j-1} - alpha_j sigma_j q_j
+// written over q_{j-1}, with the partials |w|^2 and <sigma q_j | u> (the p_j
+// projection).  The loads are separate from the arithmetic and the store so
+// that a thread can issue the loads of several groups before any store.
+template <typename real, int V>
+struct StepIn {
+  real ar[V], ai[V], xr[V], xi[V], qr[V], qi[V], ur[V], ui[V];
+};
+
+template <typename real, int V>
+__device__ __forceinline__ void step_load(const InstDesc& d, const LaunchArgs& a, long long idx, StepIn<real, V>& s) {
+  VecIO<real, V>::ldg(d.hq, idx, s.ar, s.ai);
+  for (int part = 1; part < a.hq_parts; ++part) {  // the passes' partial sums, in pass order
+    real br[V], bi[V];
+    VecIO<real, V>::ldg(d.hq, idx + part * a.hq_stride, br, bi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      s.ar[v] += br[v];
+      s.ai[v] += bi[v];
+    }
+  }
+  VecIO<real, V>::ldg(d.x, idx, s.xr, s.xi);
+  VecIO<real, V>::ldg(d.u, idx, s.ur, s.ui);
+  if (!a.first) {
+    VecIO<real, V>::ld(d.y, idx, s.qr, s.qi);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) s.qr[v] = s.qi[v] = 0;
+  }
+}
+
+template <typename real, int V>
+__device__ __forceinline__ void step_finish(const InstDesc& d, long long idx, const StepIn<real, V>& s, const real* sig,
+                                            const real* bsp, const real* coef, real* pacc) {
+  real wr[V], wi[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    wr[v] = fma(sig[v], s.ar[v], fma(-bsp[v], s.qr[v], -coef[v] * s.xr[v]));
+    wi[v] = fma(sig[v], s.ai[v], fma(-bsp[v], s.qi[v], -coef[v] * s.xi[v]));
+  }
+  VecIO<real, V>::st(d.y, idx, wr, wi);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const real vr = sig[v] * s.xr[v], vi = sig[v] * s.xi[v];
+    pacc[v * kNumPartials + 0] += wr[v] * wr[v] + wi[v] * wi[v];
+    pacc[v * kNumPartials + 1] += vr * s.ur[v] + vi * s.ui[v];
+    pacc[v * kNumPartials + 2] += vr * s.ui[v] - vi * s.ur[v];
+  }
+}
+
+// kModeStep over the groups e, e + step, ... < e_end, U groups' loads in
+// flight per thread before their stores; the partials are summed in the same
+// group order as one group at a time.
+template <typename real, int V, int U>
+__device__ __forceinline__ void step_stream(const InstDesc& d, const LaunchArgs& a, long long e, long long e_end,
+                                            long long step, const real* sig, const real* bsp, const real* coef,
+                                            real* pacc) {
+  for (; e + (U - 1) * step < e_end; e += U * step) {
+    StepIn<real, V> in[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) step_load<real, V>(d, a, e + k * step, in[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k) step_finish<real, V>(d, e + k * step, in[k], sig, bsp, coef, pacc);
+  }
+  for (; e < e_end; e += step) {
+    StepIn<real, V> in;
+    step_load<real, V>(d, a, e, in);
+    step_finish<real, V>(d, e, in, sig, bsp, coef, pacc);
+  }
+}
+
 template <typename real, int V, int MODE>
 __device__ __forceinline__ void elementwise_item(const InstDesc& d, const LaunchArgs& a, long long idx,
                                                  const real* sig, const real* bsp, const real* coef, real* pacc) {
@@ -147,39 +219,9 @@ __device__ __forceinline__ void elementwise_item(const InstDesc& d, const Launch
       pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
     }
   } else if (MODE == kModeStep) {  // w = sigma hq - bsp q_{j-1} - alpha sigma q_j; partials |w|^2, p
-    real ar[V], ai[V], xr[V], xi[V], qr[V], qi[V], ur[V], ui[V];
-    VecIO<real, V>::ldg(d.hq, idx, ar, ai);
-    for (int part = 1; part < a.hq_parts; ++part) {  // the passes' partial sums, in pass order
-      real br[V], bi[V];
-      VecIO<real, V>::ldg(d.hq, idx + part * a.hq_stride, br, bi);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        ar[v] += br[v];
-        ai[v] += bi[v];
-      }
-    }
-    VecIO<real, V>::ldg(d.x, idx, xr, xi);
-    VecIO<real, V>::ldg(d.u, idx, ur, ui);
-    if (!a.first) {
-      VecIO<real, V>::ld(d.y, idx, qr, qi);
-    } else {
-#pragma unroll
-      for (int v = 0; v < V; ++v) qr[v] = qi[v] = 0;
-    }
-    real wr[V], wi[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      wr[v] = fma(sig[v], ar[v], fma(-bsp[v], qr[v], -coef[v] * xr[v]));
-      wi[v] = fma(sig[v], ai[v], fma(-bsp[v], qi[v], -coef[v] * xi[v]));
-    }
-    VecIO<real, V>::st(d.y, idx, wr, wi);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
-      pacc[v * kNumPartials + 0] += wr[v] * wr[v] + wi[v] * wi[v];
-      pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];
-      pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
-    }
+    StepIn<real, V> in;
+    step_load<real, V>(d, a, idx, in);
+    step_finish<real, V>(d, idx, in, sig, bsp, coef, pacc);
   } else if (MODE == kModeUpdate) {
     real wr[V], wi[V], xr[V], xi[V];
     VecIO<real, V>::ld(d.y, idx, wr, wi);

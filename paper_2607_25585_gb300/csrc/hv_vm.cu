@@ -584,11 +584,15 @@ __global__ void __launch_bounds__(256) vm_stream_kernel(const __grid_constant__ 
     for (int k = 0; k < V * kNumPartials; ++k) pacc[k] = 0;
     const long long step = (long long)bd * V;
     long long e = e0 + (long long)threadIdx.x * V;
-    for (; e + step < e_end; e += 2 * step) {
-      elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
-      elementwise_item<real, V, MODE>(d, a, e + step, sig, bsp, coef, pacc);
+    if (MODE == kModeStep) {
+      step_stream<real, V, 4>(d, a, e, e_end, step, sig, bsp, coef, pacc);
+    } else {
+      for (; e + step < e_end; e += 2 * step) {
+        elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
+        elementwise_item<real, V, MODE>(d, a, e + step, sig, bsp, coef, pacc);
+      }
+      if (e < e_end) elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
     }
-    if (e < e_end) elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       real t = 0;

@@ -177,11 +177,15 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
       const long long e_end = min(row0 + a.rows_per_tile, d.dim) * a.R;
       const long long step = (long long)blockDim.x * V;
       long long e = row0 * a.R + (long long)threadIdx.x * V;
-      for (; e + step < e_end; e += 2 * step) {
-        elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
-        elementwise_item<real, V, MODE>(d, a, e + step, sig, bsp, coef, pacc);
+      if (MODE == kModeStep) {
+        step_stream<real, V, 4>(d, a, e, e_end, step, sig, bsp, coef, pacc);
+      } else {
+        for (; e + step < e_end; e += 2 * step) {
+          elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
+          elementwise_item<real, V, MODE>(d, a, e + step, sig, bsp, coef, pacc);
+        }
+        if (e < e_end) elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
       }
-      if (e < e_end) elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
     } else {
     const int items = a.rows_per_tile * C;
     for (int item = threadIdx.x; item < items; item += blockDim.x) {

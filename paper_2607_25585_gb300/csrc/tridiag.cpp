@@ -7,9 +7,12 @@
 // U_0n (the weight <n|r>) and sum_j conj(p_j) U_jn (= <r|O|n>), so instead of
 // accumulating the whole of U the plane rotations are applied to those row
 // vectors only: O(M^2) per run instead of O(M^3).
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <thread>
 #include <vector>
 
 #include "ftlm_internal.h"
@@ -17,6 +20,36 @@
 namespace ftlm {
 
 namespace {
+
+// sqrt(a^2 + b^2): the plain formula where the squares can neither overflow
+// nor underflow, the library's careful hypot elsewhere
+inline double norm2(double a, double b) {
+  const double m = std::max(std::fabs(a), std::fabs(b));
+  if (m < 1e150 && m > 1e-150) return std::sqrt(a * a + b * b);
+  return std::hypot(a, b);
+}
+
+// fn(i) for i in [0, n) on up to hardware_concurrency host threads (the
+// caller's thread works too); each i runs exactly once
+template <typename Fn>
+void parallel_for(int n, Fn&& fn) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nth = std::min(std::min(n, hw), 32);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int i; (i = next.fetch_add(1)) < n;) fn(i);
+  };
+  std::vector<std::thread> pool;
+  for (int k = 1; k < nth; ++k) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {
+      break;  // fewer threads: the others take the remaining items
+    }
+  }
+  work();
+  for (auto& t : pool) t.join();
+}
 
 // Eigenvalues of tridiag(d, e) (d[0..m-1], e[0..m-2] off-diagonal) with the
 // rotations applied to the rows z[k][0..m-1], k < nz.  Returns false if the
@@ -37,14 +70,14 @@ bool ql_implicit(int m, double* d, double* e_in, int nz, double** z) {
       if (++iter > 100) return false;
       // shift from the leading 2x2 block
       double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = std::hypot(g, 1.0);
+      double r = norm2(g, 1.0);
       g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
       double s = 1.0, c = 1.0, p = 0.0;
       int i = mm - 1;
       bool deflated = false;
       for (; i >= l; --i) {
         const double f = s * e[i], b = c * e[i];
-        r = std::hypot(f, g);
+        r = norm2(f, g);
         e[i + 1] = r;
         if (r == 0.0) {  // underflow: split the matrix here
           d[i + 1] -= p;
@@ -91,13 +124,15 @@ ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const
     std::vector<double> eps, w0, qr, qi;  // Ritz values, U_0n, Re/Im of sum_j conj(p_j) U_jn
   };
   std::vector<Run> runs(R);
-  double E0 = std::numeric_limits<double>::infinity();
-  for (int r = 0; r < R; ++r) {
-    const int m = M_eff[r];
-    if (m < 1 || m > M) {
+  for (int r = 0; r < R; ++r)
+    if (M_eff[r] < 1 || M_eff[r] > M) {
       msg = "M_eff out of range";
       return FTLM_ERR_INVALID_ARG;
     }
+  // the runs' eigenproblems are independent: one per host thread
+  std::vector<int> bad(R, 0);  // 1: non-finite coefficient, 2: no convergence
+  parallel_for(R, [&](int r) {
+    const int m = M_eff[r];
     Run& run = runs[r];
     run.eps.assign(alpha + (size_t)r * M, alpha + (size_t)r * M + m);
     std::vector<double> e(m > 1 ? m - 1 : 1, 0.0);
@@ -112,18 +147,27 @@ ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const
     }
     for (int j = 0; j < m; ++j)
       if (!std::isfinite(run.eps[j]) || (j + 1 < m && !std::isfinite(e[j]))) {
-        msg = "non-finite Lanczos coefficient in run " + std::to_string(r);
-        return FTLM_ERR_NUMERICAL;
+        bad[r] = 1;
+        return;
       }
     double* rows[3] = {run.w0.data(), run.qr.data(), run.qi.data()};
-    if (!ql_implicit(m, run.eps.data(), e.data(), 3, rows)) {
+    if (!ql_implicit(m, run.eps.data(), e.data(), 3, rows)) bad[r] = 2;
+  });
+  double E0 = std::numeric_limits<double>::infinity();
+  for (int r = 0; r < R; ++r) {
+    if (bad[r] == 1) {
+      msg = "non-finite Lanczos coefficient in run " + std::to_string(r);
+      return FTLM_ERR_NUMERICAL;
+    }
+    if (bad[r] == 2) {
       msg = "tridiagonal eigensolver did not converge (run " + std::to_string(r) + ")";
       return FTLM_ERR_NUMERICAL;
     }
-    for (int n = 0; n < m; ++n) E0 = std::min(E0, run.eps[n]);
+    for (double v : runs[r].eps) E0 = std::min(E0, v);
   }
   res->E0 = E0;
-  for (int t = 0; t < nT; ++t) {
+  // the temperatures are independent too (each sums the runs in order)
+  parallel_for(nT, [&](int t) {
     const double b = 1.0 / T[t];
     double z = 0.0, e1 = 0.0, orr = 0.0, oi = 0.0;
     for (const Run& run : runs)
@@ -147,7 +191,7 @@ ftlm_status host_sums(int R, int M, const int* M_eff, const double* alpha, const
     if (res->C) res->C[t] = b * b * var / z;
     if (res->M_B) res->M_B[t] = -g * orr / z;
     if (res->M_B_imag) res->M_B_imag[t] = -g * oi / z;
-  }
+  });
   return FTLM_OK;
 }
 
@@ -170,14 +214,15 @@ ftlm_status host_sums_sym(int R, int M, const int* M_eff, const double* alpha, c
     std::vector<double> eps, U;  // U[k * m + n] = U_kn
   };
   std::vector<Run> runs(R);
-  double E0 = std::numeric_limits<double>::infinity();
-  for (int r = 0; r < R; ++r) {
-    Run& run = runs[r];
-    const int m = run.m = M_eff[r];
-    if (m < 1 || m > M) {
+  for (int r = 0; r < R; ++r)
+    if (M_eff[r] < 1 || M_eff[r] > M) {
       msg = "M_eff out of range";
       return FTLM_ERR_INVALID_ARG;
     }
+  std::vector<int> bad(R, 0);
+  parallel_for(R, [&](int r) {
+    Run& run = runs[r];
+    const int m = run.m = M_eff[r];
     run.eps.assign(alpha + (size_t)r * M, alpha + (size_t)r * M + m);
     std::vector<double> e(m > 1 ? m - 1 : 1, 0.0);
     for (int j = 0; j + 1 < m; ++j) e[j] = beta[(size_t)r * M + j];
@@ -187,13 +232,17 @@ ftlm_status host_sums_sym(int R, int M, const int* M_eff, const double* alpha, c
       run.U[(size_t)k * m + k] = 1.0;
       rows[k] = run.U.data() + (size_t)k * m;
     }
-    if (!ql_implicit(m, run.eps.data(), e.data(), m, rows.data())) {
+    if (!ql_implicit(m, run.eps.data(), e.data(), m, rows.data())) bad[r] = 1;
+  });
+  double E0 = std::numeric_limits<double>::infinity();
+  for (int r = 0; r < R; ++r) {
+    if (bad[r]) {
       msg = "tridiagonal eigensolver did not converge (run " + std::to_string(r) + ")";
       return FTLM_ERR_NUMERICAL;
     }
-    for (int n = 0; n < m; ++n) E0 = std::min(E0, run.eps[n]);
+    for (double v : runs[r].eps) E0 = std::min(E0, v);
   }
-  for (int t = 0; t < nT; ++t) {
+  parallel_for(nT, [&](int t) {
     const double b = 1.0 / T[t];
     double den = 0.0, nre = 0.0, nim = 0.0;
     for (int r = 0; r < R; ++r) {
@@ -220,7 +269,7 @@ ftlm_status host_sums_sym(int R, int M, const int* M_eff, const double* alpha, c
     }
     MB_sym[t] = -g * nre / den;
     if (MB_sym_imag) MB_sym_imag[t] = -g * nim / den;
-  }
+  });
   return FTLM_OK;
 }
 

@@ -73,6 +73,42 @@ def test_sums_reject_bad_input():
         F.sums(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)), [2], 8, 2.0, [0.0])
 
 
+def test_sums_many_runs_deterministic_and_per_run(rng):
+    """The runs' eigenproblems and the temperatures are spread over host
+    threads: the result must not depend on that (bitwise equal on repeat and
+    equal to the runs merged one at a time in the same order), and an error
+    names the run it comes from."""
+    R, M = 40, 60
+    # weak disorder (extended Ritz vectors), so that every temperature's
+    # weights are well conditioned
+    a = 0.1 * rng.normal(size=(R, M))
+    b = 1.0 + 0.1 * np.abs(rng.normal(size=(R, M)))
+    p = rng.normal(size=(R, M)) + 1j * rng.normal(size=(R, M))
+    me = rng.integers(1, M + 1, size=R).astype(np.int32)
+    T = np.geomspace(0.05, 50.0, 33)
+    r1 = F.sums(a, b, p, me, 4096, 2.0, T)
+    r2 = F.sums(a, b, p, me, 4096, 2.0, T)
+    for k in ("lnZ", "E", "C", "M_B", "M_B_imag"):
+        assert np.array_equal(r1[k], r2[k]), k
+    # Eqs. 4-5 from the per-run Ritz data, merged by hand
+    ev = [np.linalg.eigh(np.diag(a[r, :me[r]]) + np.diag(b[r, :me[r] - 1], 1) + np.diag(b[r, :me[r] - 1], -1))
+          for r in range(R)]
+    E0 = min(w.min() for w, _ in ev)
+    for t, Tt in enumerate(T):
+        z = e1 = orr = 0.0
+        for r, (w, U) in enumerate(ev):
+            bz = np.exp(-(w - E0) / Tt)
+            z += np.sum(U[0] ** 2 * bz)
+            e1 += np.sum(U[0] ** 2 * bz * w)
+            orr += np.sum(bz * U[0] * (np.conj(p[r, :me[r]]) @ U).real)
+        assert abs(r1["E"][t] - e1 / z) < 1e-9 * max(1.0, abs(e1 / z)), t
+        assert abs(r1["M_B"][t] + 2.0 * orr / z) < 1e-9 * max(1.0, abs(orr / z)), t
+    bad = a.copy()
+    bad[27, 0] = np.nan
+    with pytest.raises(F.FtlmError, match="run 27"):
+        F.sums(bad, b, p, me, 4096, 2.0, T)
+
+
 def test_sums_sym_match_oracle(rng):
     """ftlm_sums_sym (host-only) reproduces the oracle's symmetric estimator
     from the same per-vector data."""
