@@ -51,7 +51,7 @@ typedef enum {
   FTLM_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
   FTLM_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the code) */
   FTLM_ERR_TIMEOUT = 4,       /* reserved: a bounded device wait gave up */
-  FTLM_ERR_UNSUPPORTED = 5,   /* valid request outside what this build supports */
+  FTLM_ERR_UNSUPPORTED = 5,   /* valid request outside what the library supports */
   FTLM_ERR_NUMERICAL = 6      /* NaN/Inf in the Lanczos scalars or the eigensolver */
 } ftlm_status;
 
