@@ -29,6 +29,13 @@
 //   SC'11) + Box-Muller;  each r normalised to 1;  Z returned as ln Z with the
 //   lowest Ritz value E0 factored out;  M_B = -g <B^.S> in units of mu_B.
 //
+// Pins (tests/test_oracle_*.py) tie every function to closed forms, the dense
+// definition, LAPACK and exact limits.  A finite-R FTLM estimate differs from
+// the exact thermodynamics by a statistical error, so at finite R it is pinned
+// only through its exact limits (all basis vectors as start vectors; full
+// Krylov depth, where it equals the stochastic trace of Eq. 1): parity
+// unpinned at tolerance level for finite R against exact diagonalisation.
+//
 // Everything is double precision and deliberately unoptimised: the matvec is a
 // column scatter (for each source state nu, apply every term of H to |nu>),
 // the tridiagonal eigenproblem is solved by cyclic Jacobi on the dense matrix.
