@@ -119,3 +119,34 @@ def test_sums_sym_match_oracle(rng):
     mb, mbi = F.sums_sym(o["alpha"], o["beta"], o["O"], o["M_eff"], w["g"], T)
     assert np.allclose(mb, o["M_B_sym"], rtol=1e-11, atol=1e-13)
     assert np.allclose(mbi, o["M_B_sym_imag"], rtol=1e-9, atol=1e-12)
+
+
+def test_sums_sym_many_runs_match_definition(rng):
+    """ftlm_sums_sym with the runs and temperatures spread over host threads:
+    bitwise equal on repeat, and equal to Eqs. E-2-G/H written out with numpy
+    (y = U e^{-beta eps/2} U_0, num = y^T O y, den = sum e^{-beta eps} U_0^2)."""
+    R, M = 24, 16
+    a = 0.1 * rng.normal(size=(R, M))
+    b = 1.0 + 0.1 * np.abs(rng.normal(size=(R, M)))
+    O = rng.normal(size=(R, M, M)) + 1j * rng.normal(size=(R, M, M))
+    O = 0.5 * (O + np.conj(np.transpose(O, (0, 2, 1))))  # Hermitian, as <v_i|O|v_j> is
+    me = rng.integers(2, M + 1, size=R).astype(np.int32)
+    T = np.geomspace(0.1, 20.0, 17)
+    g = 2.0
+    mb1, mbi1 = F.sums_sym(a, b, O, me, g, T)
+    mb2, mbi2 = F.sums_sym(a, b, O, me, g, T)
+    assert np.array_equal(mb1, mb2) and np.array_equal(mbi1, mbi2)
+    ev = [np.linalg.eigh(np.diag(a[r, :me[r]]) + np.diag(b[r, :me[r] - 1], 1) + np.diag(b[r, :me[r] - 1], -1))
+          for r in range(R)]
+    E0 = min(w.min() for w, _ in ev)
+    for t, Tt in enumerate(T):
+        num, den = 0.0, 0.0
+        for r, (w, U) in enumerate(ev):
+            m = me[r]
+            h = np.exp(-0.5 * (w - E0) / Tt)
+            y = U @ (h * U[0])
+            num += y @ O[r, :m, :m] @ y
+            den += np.sum(h * h * U[0] ** 2)
+        ref = -g * num / den
+        assert abs(mb1[t] - ref.real) < 1e-10 * max(1.0, abs(ref)), t
+        assert abs(mbi1[t] - ref.imag) < 1e-10 * max(1.0, abs(ref)), t
