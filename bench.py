@@ -476,9 +476,15 @@ def cpu_baseline(args, steps=None):
     t0 = time.perf_counter()
     oracle.ftlm(s, R=cores, M=M, T=W.temperatures(), seed=spec["seed"])
     dt = time.perf_counter() - t0
+    # the same on one host thread (one vector: the oracle threads over vectors)
+    t0 = time.perf_counter()
+    oracle.ftlm(s, R=1, M=M, T=W.temperatures(), seed=spec["seed"])
+    dt1 = time.perf_counter() - t0
     return {"value": s.dim * cores * M / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{cores} vectors x {M} Lanczos steps of the full d={s.dim} system "
-                      f"(plain C++ FP64 oracle, OpenMP over vectors), {dt:.1f} s"}
+                      f"(plain C++ FP64 oracle, OpenMP over vectors), {dt:.1f} s",
+            "single_thread": {"value": s.dim * M / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"1 vector x {M} Lanczos steps of the same system, {dt1:.1f} s"}}
 
 
 def run_reference(args):
