@@ -150,3 +150,23 @@ def test_sums_sym_many_runs_match_definition(rng):
         ref = -g * num / den
         assert abs(mb1[t] - ref.real) < 1e-10 * max(1.0, abs(ref)), t
         assert abs(mbi1[t] - ref.imag) < 1e-10 * max(1.0, abs(ref)), t
+
+
+@pytest.mark.parametrize("lam", [1e-170, 1e-3, 1e3, 1e170])
+def test_sums_scale_invariance(rng, lam):
+    """Scaling alpha, beta and T by the same factor scales E by it and leaves
+    ln Z and M_B unchanged (Eqs. 4-5 depend on (eps - E0) / T only).  At
+    1e+-170 the squares in the eigensolver's rotations would overflow or
+    underflow, so this also checks that they are formed without squaring
+    there."""
+    R, M = 6, 40
+    a = 0.1 * rng.normal(size=(R, M))
+    b = 1.0 + 0.1 * np.abs(rng.normal(size=(R, M)))
+    p = rng.normal(size=(R, M)) + 1j * rng.normal(size=(R, M))
+    me = np.full(R, M, dtype=np.int32)
+    T = np.geomspace(0.1, 10.0, 7)
+    r1 = F.sums(a, b, p, me, 4096, 2.0, T)
+    r2 = F.sums(lam * a, lam * b, p, me, 4096, 2.0, lam * T)
+    assert np.allclose(r2["E"] / lam, r1["E"], rtol=1e-11, atol=1e-13)
+    assert np.allclose(r2["lnZ"], r1["lnZ"], rtol=1e-11, atol=1e-11)
+    assert np.allclose(r2["M_B"], r1["M_B"], rtol=1e-10, atol=1e-12)
