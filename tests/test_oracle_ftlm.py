@@ -175,3 +175,24 @@ def test_random_vector_ftlm_converges_statistically():
     ex = dense.thermo_exact(s, T)
     hi = T >= 1.0
     assert np.max(np.abs(r["E"][hi] - ex["E"][hi]) / np.abs(ex["E"][hi]).max()) < 0.1
+
+
+def test_high_temperature_limits():
+    """T -> infinity with every term of Eq. (3): E -> tr H / d =
+    sum_i d_i s_i(s_i+1)/3 (exchange, dipolar and Zeeman terms are traceless),
+    with E - tr H / d = -Var(H) / T + O(1/T^2); and the Curie law
+    M_B T -> g^2 mu_B |B| sum_i s_i(s_i+1)/3, since to first order in beta
+    <B^.S> = -beta tr((B^.S) H) / d and only the Zeeman term contributes."""
+    w = random_system(np.random.default_rng(2607), [1, 2, 1, 3], scale=6.0)
+    s = oracle_system(w)
+    sv = np.asarray(w["two_s"]) / 2.0
+    Tk = np.array([1e6, 1e7])
+    r = oracle.ftlm(s, R=s.dim, M=s.dim, T=Tk, start="basis", reorth=True)
+    e1 = np.sum(w["d_ion"] * sv * (sv + 1) / 3)
+    dev = (r["E"] - e1) * Tk
+    assert dev[0] < 0 and dev[1] < 0                      # -Var(H) < 0
+    assert abs(dev[0] / dev[1] - 1) < 1e-3                 # the 1/T term
+    assert np.all(np.abs(r["E"] - e1) < 1e-3 * max(1.0, abs(e1)))
+    curie = w["g"] ** 2 * MU_B * np.linalg.norm(w["B"]) * np.sum(sv * (sv + 1) / 3)
+    assert abs(r["M_B"][0] * Tk[0] / curie - 1) < 1e-4
+    assert abs(r["M_B"][1] * Tk[1] / curie - 1) < 1e-5
