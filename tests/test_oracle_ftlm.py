@@ -196,3 +196,21 @@ def test_high_temperature_limits():
     curie = w["g"] ** 2 * MU_B * np.linalg.norm(w["B"]) * np.sum(sv * (sv + 1) / 3)
     assert abs(r["M_B"][0] * Tk[0] / curie - 1) < 1e-4
     assert abs(r["M_B"][1] * Tk[1] / curie - 1) < 1e-5
+
+
+def test_thermodynamics_invariant_under_rotation_and_field_reversal():
+    """Rotating positions, axes and B together, or reversing B (time
+    reversal), leaves ln Z, E, C and M_B unchanged: the oracle's FTLM in exact
+    mode on the three systems (M_B is measured along B^ of each)."""
+    rng = np.random.default_rng(7)
+    w = random_system(rng, [1, 2, 1, 2])
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    Rm = q * np.sign(np.linalg.det(q))                    # a proper rotation
+    variants = [w, dict(w, pos=w["pos"] @ Rm.T, e_axes=w["e_axes"] @ Rm.T, B=Rm @ w["B"]), dict(w, B=-w["B"])]
+    res = []
+    for v in variants:
+        s = oracle_system(v)
+        res.append(oracle.ftlm(s, R=s.dim, M=s.dim, T=T, start="basis", reorth=True))
+    for r in res[1:]:
+        for k in ("lnZ", "E", "C", "M_B"):
+            assert _rel(r[k], res[0][k], 1e-6) < 1e-10, k
