@@ -211,7 +211,7 @@ def run_ours(args):
             "config": {"workload": f"open 4x5 s=1/2 lattice, all-pairs dipolar, d={d}, R={R} vectors, M={M} "
                                    "Lanczos steps, complex64 vectors, FP32 matvec, FP64 scalars/eigensolve/sums",
                        "d": d, "R": R, "M": M, "global_batch_vectors": R * ws, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (three 512 MB vector blocks)"},
+                       "l2": "inputs larger than L2 (four 512 MB vector blocks: q_j, q_{j-1}, H q_j, u)"},
             "hbm_roof_frac": value / ws * 32 / (hbm * 1e9),
             "roofline": {"bound": "alu", "kernel": kname,
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
