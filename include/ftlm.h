@@ -285,7 +285,11 @@ ftlm_status ftlm_run_batch(int n, const ftlm_system* const* systems, const ftlm_
  * data of R vectors (as returned in ftlm_result, [R][M] row-major) computes
  * E0, ln Z, E, C, M_B and M_B_imag.  Used to merge vectors run on several
  * processes: gather alpha, beta, p, M_eff from all of them and call this
- * once.  Host-only: needs no GPU.
+ * once.  Host-only: needs no GPU.  The R tridiagonal eigenproblems and the
+ * temperatures are spread over up to min(R, hardware threads, 32) host
+ * threads created and joined inside the call; the result does not depend on
+ * their number (each sum runs in a fixed order).  ftlm_run, ftlm_run_batch
+ * and ftlm_sums_sym do the same for their host part.
  *  dim  Hilbert-space dimension d; g  g factor.
  */
 ftlm_status ftlm_sums(int R, int M, const int* M_eff, const double* alpha, const double* beta, const double* p,
