@@ -202,6 +202,7 @@ def run_ours(args):
         else:
             kname = "rows_kernel<float,2,Lanczos> (general gather with the fused step)"
         traffic = measured_traffic(shp)
+        precision = None if args.no_precision else precision_legs(F, T, stream, args, s, spec, results)
         plain = None if args.no_plain else plain_fp64(F, s, T, spec, stream, args)
         extra = None if args.no_extra else extra_workloads(F, T, stream, args)
         line = {
@@ -221,11 +222,14 @@ def run_ours(args):
             "hbm": {"bytes_per_sv": 32, "peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                     "frac": value / ws * 32 / (hbm * 1e9)},
             "plain_fp64": plain,
+            "fp32_vs_fp64": precision,
             "other_workloads": extra,
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
         }
         if plain and plain.get("value"):
             line["speedup_vs_plain_fp64"] = value / ws / plain["value"]
+        if precision and precision.get("lattice4x5", {}).get("fp64_value"):
+            line["speedup_vs_batched_fp64"] = value / ws / precision["lattice4x5"]["fp64_value"]
         if args.cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args)
     s.close()
@@ -255,6 +259,66 @@ def measured_traffic(shape):
             continue
         return rec["bytes_per_launch"]
     return None
+
+
+def per_t_errors(a, b, T, floor=1e-3):
+    """Relative error of every thermodynamic result of run a against run b at
+    each temperature, with a floor of `floor` times the quantity's maximum
+    over T (quantities that pass through zero), and its maximum over
+    T >= 0.1 K."""
+    out = {}
+    cold = T >= 0.1
+    for k in ("lnZ", "E", "C", "M_B"):
+        x, y = np.asarray(a[k]), np.asarray(b[k])
+        e = np.abs(x - y) / np.maximum(np.abs(y), floor * np.max(np.abs(y)))
+        out[k] = {"max_T_ge_0.1": float(e[cold].max()), "max_all_T": float(e.max()),
+                  "per_T": [float(v) for v in e]}
+    out["max_T_ge_0.1"] = max(out[k]["max_T_ge_0.1"] for k in ("lnZ", "E", "C", "M_B"))
+    return out
+
+
+def timed_run(F, s, stream, **kw):
+    import torch
+    F.run(s, stream=stream, **kw)  # captures the graph
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = F.run(s, stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return res, e0.elapsed_time(e1)
+
+
+def precision_legs(F, T, stream, args, s_head, spec_head, res_head):
+    """FP32 (complex64 vectors, FP32 matvec, FP64 scalars) against FP64
+    (complex128, the same kernels in double) on the same random vectors,
+    per temperature: the 4x5 lattice at its full R = 64, M = 200 (the c64 run
+    is the headline's last timed run; the c128 run of the whole block is also
+    the batched-FP64 throughput) and the 2x13 ladder at R = 4, M = 300 (both
+    timed as full runs)."""
+    out = {}
+    R, M = spec_head["R"], args.M or spec_head["M"]
+    d = s_head.dim
+    r128, ms128 = timed_run(F, s_head, stream, R=R, M=M, T=T, seed=spec_head["seed"], dtype="c128")
+    out["lattice4x5"] = {"R": R, "M": M, "d": d, "fp64_value": d * R * M / (ms128 / 1e3), "fp64_ms": ms128,
+                         "fp64_launch_shape": r128["shape"], "unit": UNIT,
+                         "errors_vs_fp64": per_t_errors(res_head, r128, T),
+                         "note": "same Philox vectors; FP64 = complex128 block of all 64 vectors (batched FP64)"}
+    if not args.no_ladder_precision:
+        spec = W.WORKLOADS["ladder2x13"]
+        s = F.System.from_dict(spec["system"]())
+        R, M = spec["R"], spec["M"]
+        d = s.dim
+        r64, ms64 = timed_run(F, s, stream, R=R, M=M, T=T, seed=spec["seed"], dtype="c64", time_kernels=True)
+        r128, ms128 = timed_run(F, s, stream, R=R, M=M, T=T, seed=spec["seed"], dtype="c128")
+        out["ladder2x13"] = {"R": R, "M": M, "d": d, "fp32_value": d * R * M / (ms64 / 1e3), "fp32_ms": ms64,
+                             "fp64_value": d * R * M / (ms128 / 1e3), "fp64_ms": ms128, "unit": UNIT,
+                             "fp32_hv_ms_per_launch": r64["hv_ms"] / max(1, r64["hv_launches"]),
+                             "fp32_launch_shape": r64["shape"], "fp64_launch_shape": r128["shape"],
+                             "errors_vs_fp64": per_t_errors(r64, r128, T)}
+        s.close()
+    out["T"] = [float(t) for t in T]
+    return out
 
 
 def plain_fp64(F, s, T, spec, stream, args):
@@ -289,7 +353,7 @@ def extra_workloads(F, T, stream, args):
     systems = [F.System.from_dict(w) for w in spec["system"]()]
     R, M = spec["R"], spec["M"]
     kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True)
-    F.run_batch(systems, autotune=args.autotune, **kw)
+    F.run_batch(systems, autotune=True, **kw)  # the autotuner picks the launch shape (kept for the timed run)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -300,7 +364,8 @@ def extra_workloads(F, T, stream, args):
     sv = sum(s.dim for s in systems) * R * M
     out["chains_s1_x24"] = {"value": sv / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R,
                             "instances": len(systems), "hv_ms_per_launch": res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
-                            "launch_shape": res[0]["shape"], "note": "one graph for all 24 instances; general kernel"}
+                            "launch_shape": res[0]["shape"], "autotuned": True,
+                            "note": "one graph for all 24 instances; shape chosen by the autotuner"}
     for s in systems:
         s.close()
     spec = W.WORKLOADS["ladder2x13"]
@@ -580,6 +645,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2, help="Lanczos steps of the oracle sample")
     ap.add_argument("--plain-chains", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 legs")
+    ap.add_argument("--no-ladder-precision", action="store_true", help="skip the 2x13 ladder in the FP32-vs-FP64 legs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and ladder measurements")
     ap.add_argument("--ladder-steps", type=int, default=20)

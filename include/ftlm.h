@@ -219,6 +219,14 @@ typedef struct {
   int symmetric;         /* 1 = also the symmetric estimator of M_B (sFTLM, Eqs. E-2-G/H):
                             keeps all M Lanczos vectors on the device (M x R x dim values of
                             dtype), forms O_ij = <v_i|u.S|v_j> per vector; one system only */
+  int reorth;            /* 0 = none (the three-term recurrence of Sec. II.C, two predecessor
+                            vectors: the hot path).  1 = full re-orthogonalisation, the optional
+                            step of Sec. II.C: after w = H v_j - alpha_j v_j - beta_j v_{j-1},
+                            w -= sum_{k<=j} v_k <v_k|w> is applied twice before beta_{j+1} = |w|.
+                            Keeps all M Lanczos vectors on the device (M x R x dim values of
+                            dtype, as symmetric), runs the general row kernel, and moves
+                            O(M^2 R dim) bytes per run: meant for small dim.  ftlm_run only
+                            (ftlm_run_batch returns FTLM_ERR_UNSUPPORTED). */
 } ftlm_run_params;
 
 typedef struct {

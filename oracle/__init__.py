@@ -90,6 +90,8 @@ def _load():
                                           pd, pd, pd, pd, pd, pd]
         _lib.oracle_ftlm.argtypes = [P(_CSystem), i32, i32, u64, u64, i32, i64, pd, i32, d, pd,
                                      pd, i32, pd, pd, pd, pd, pd, pd, pd, pd, pd, P(i32)]
+        _lib.oracle_ftlm_tridiag.argtypes = [P(_CSystem), i32, i32, u64, u64, i32, i64, pd, i32, d, pd,
+                                             pd, pd, pd, P(i32)]
         _lib.oracle_num_threads.restype = i32
     return _lib
 
@@ -334,6 +336,25 @@ def ftlm(sys: System, R: int, M: int, T=None, seed: int = 0, vec_offset: int = 0
     assert rc == 0, "oracle_ftlm failed"
     out.update(E0=float(E0[0]), alpha=a, beta=b, p=p, M_eff=me, T=T)
     return out
+
+
+def ftlm_tridiag(sys: System, R: int, M: int, seed: int = 0, vec_offset: int = 0, start: str = "random",
+                 basis_offset: int = 0, reorth: bool = False, tol: float = 1e-12, direction=None):
+    """The Lanczos half of ``ftlm`` alone (R recurrences, one host thread
+    each): alpha, beta, p [R][M] and M_eff [R], no eigensolve or sums."""
+    lib = _load()
+    mode = {"random": 0, "basis": 1, "pairs": 3}[start]
+    a = np.zeros((R, M))
+    b = np.zeros((R, M))
+    p = np.zeros((R, M), dtype=np.complex128)
+    me = np.zeros(R, dtype=np.int32)
+    u = None if direction is None else np.ascontiguousarray(direction, dtype=np.float64)
+    cs = sys.c()
+    rc = lib.oracle_ftlm_tridiag(ctypes.byref(cs), R, M, seed, vec_offset, mode, basis_offset, None, int(reorth), tol,
+                                 _pd(u), _pd(a), _pd(b), _pd(p.view(np.float64)),
+                                 me.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    assert rc == 0, "oracle_ftlm_tridiag failed"
+    return {"alpha": a, "beta": b, "p": p, "M_eff": me}
 
 
 def sftlm(sys: System, R: int, M: int, T=None, seed: int = 0, vec_offset: int = 0, start: str = "random",

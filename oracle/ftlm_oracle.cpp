@@ -23,7 +23,7 @@
 //     figures of Sec. III), Theta = exp(-i pi S^y) K with K the complex
 //     conjugation in the S^z product basis.
 //
-// Readings where the paper is silent (each is listed in the design notes):
+// Readings where the paper is silent (this oracle and the CUDA library both take them):
 //   basis index mu = sum_i a_i * prod_{k<i} q_k, site 0 least significant,
 //   digit a_i = m_i + s_i;  random numbers: Philox4x32-10 (Salmon et al.,
 //   SC'11) + Box-Muller;  each r normalised to 1;  Z returned as ln Z with the
@@ -623,10 +623,12 @@ int oracle_ftlm_sums(int R, int maxM, const int* M_eff, const double* alpha, con
   if (R <= 0 || maxM <= 0 || nT <= 0) return -1;
   std::vector<std::vector<double>> ev(R), u0(R);
   std::vector<std::vector<cplx>> q(R);
-  double E0 = INFINITY;
+  for (int r = 0; r < R; ++r)
+    if (M_eff[r] <= 0 || M_eff[r] > maxM) return -1;
+  // the R eigenproblems are independent: one host thread each (no shared writes)
+#pragma omp parallel for schedule(dynamic, 1)
   for (int r = 0; r < R; ++r) {
     const int m = M_eff[r];
-    if (m <= 0 || m > maxM) return -1;
     std::vector<double> U((size_t)m * m);
     ev[r].resize(m);
     jacobi_tridiag(m, alpha + (size_t)r * maxM, beta + (size_t)r * maxM, ev[r].data(), U.data());
@@ -638,9 +640,11 @@ int oracle_ftlm_sums(int R, int maxM, const int* M_eff, const double* alpha, con
       cplx acc = 0.0;
       for (int j = 0; j < m; ++j) acc += U[(size_t)j * m + nn] * std::conj(pr[j]);  // <r|O|n>
       q[r][nn] = acc;
-      E0 = std::min(E0, ev[r][nn]);
     }
   }
+  double E0 = INFINITY;
+  for (int r = 0; r < R; ++r)
+    for (double e : ev[r]) E0 = std::min(E0, e);
   for (int t = 0; t < nT; ++t) {
     const double b = 1.0 / T[t];
     double z = 0.0, e1 = 0.0;
@@ -673,12 +677,13 @@ int oracle_ftlm_sums(int R, int maxM, const int* M_eff, const double* alpha, con
 // Full FTLM.  start_mode: 0 = Philox random vectors (vec_offset + k),
 // 1 = basis vectors |basis_offset + k>, 2 = user block [d][R] (normalised per
 // column inside).  alpha, beta, p, M_eff: outputs [R][M] (may be NULL).
-int oracle_ftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t vec_offset, int start_mode,
-                int64_t basis_offset, const double* user_start, int reorth, double tol, const double* dir,
-                const double* T, int nT, double* lnZ, double* E, double* C, double* MB, double* MB_imag,
-                double* E0, double* alpha_out, double* beta_out, double* p_out, int* meff_out) {
+// The Lanczos half of FTLM on its own: the R recurrences (one host thread
+// each), returning their tridiagonal data alpha, beta, p [R][M] and M_eff [R].
+int oracle_ftlm_tridiag(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t vec_offset,
+                        int start_mode, int64_t basis_offset, const double* user_start, int reorth, double tol,
+                        const double* dir, double* alpha_out, double* beta_out, double* p_out, int* meff_out) {
   Model M;
-  if (!build_model(s, M) || R <= 0 || maxM <= 0 || nT <= 0) return -1;
+  if (!build_model(s, M) || R <= 0 || maxM <= 0) return -1;
   auto PL = all_pair_ladders(M);
   const double* u = dir ? dir : M.Bdir;
   std::vector<double> alpha((size_t)R * maxM, 0.0), beta((size_t)R * maxM, 0.0);
@@ -697,6 +702,25 @@ int oracle_ftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t
                       &p[(size_t)r * maxM]);
   }
   if (fail) return -1;
+  std::memcpy(alpha_out, alpha.data(), sizeof(double) * alpha.size());
+  std::memcpy(beta_out, beta.data(), sizeof(double) * beta.size());
+  std::memcpy(p_out, p.data(), sizeof(cplx) * p.size());
+  std::memcpy(meff_out, meff.data(), sizeof(int) * meff.size());
+  return 0;
+}
+
+int oracle_ftlm(const oracle_system* s, int R, int maxM, uint64_t seed, uint64_t vec_offset, int start_mode,
+                int64_t basis_offset, const double* user_start, int reorth, double tol, const double* dir,
+                const double* T, int nT, double* lnZ, double* E, double* C, double* MB, double* MB_imag,
+                double* E0, double* alpha_out, double* beta_out, double* p_out, int* meff_out) {
+  Model M;
+  if (!build_model(s, M) || R <= 0 || maxM <= 0 || nT <= 0) return -1;
+  std::vector<double> alpha((size_t)R * maxM, 0.0), beta((size_t)R * maxM, 0.0);
+  std::vector<cplx> p((size_t)R * maxM, 0.0);
+  std::vector<int> meff(R, 0);
+  if (oracle_ftlm_tridiag(s, R, maxM, seed, vec_offset, start_mode, basis_offset, user_start, reorth, tol, dir,
+                          alpha.data(), beta.data(), reinterpret_cast<double*>(p.data()), meff.data()) != 0)
+    return -1;
   int rc = oracle_ftlm_sums(R, maxM, meff.data(), alpha.data(), beta.data(), reinterpret_cast<double*>(p.data()),
                             (double)M.dim, M.g, T, nT, lnZ, E, C, MB, MB_imag, E0);
   if (alpha_out) std::memcpy(alpha_out, alpha.data(), sizeof(double) * alpha.size());

@@ -44,7 +44,7 @@ class RunParams(ctypes.Structure):
         ("user_start", ctypes.c_void_p), ("T", ctypes.POINTER(ctypes.c_double)), ("nT", ctypes.c_int),
         ("obs_dir", ctypes.POINTER(ctypes.c_double)), ("breakdown_tol", ctypes.c_double),
         ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int), ("stream", ctypes.c_void_p),
-        ("symmetric", ctypes.c_int),
+        ("symmetric", ctypes.c_int), ("reorth", ctypes.c_int),
     ]
 
 
@@ -152,6 +152,46 @@ def _stream(s, *blocks):
     return int(s.cuda_stream)
 
 
+_ELEMENT_BYTES = {C128: 16, C64: 8}
+
+
+def _check_block(t, dim: int, nvec: int, dtype, name="block"):
+    """Checks a device block before its pointer goes to the library: for a
+    tensor (an object with ``data_ptr()``), that it is on a CUDA device,
+    contiguous, of the element size of ``dtype`` and holds at least
+    dim * nvec elements; a raw pointer (int) is the caller's responsibility.
+    Raises FtlmError(FTLM_ERR_INVALID_ARG) without calling the library."""
+    if t is None or isinstance(t, int):
+        return
+    code = _DTYPES.get(dtype)
+    if code is None:
+        raise FtlmError(1, f"{name}: unknown dtype {dtype!r}")
+    dev = getattr(t, "device", None)
+    if dev is not None and getattr(dev, "type", "cuda") != "cuda":
+        raise FtlmError(1, f"{name}: a device block is needed, got a tensor on {dev}")
+    if hasattr(t, "is_contiguous") and not t.is_contiguous():
+        raise FtlmError(1, f"{name}: the block must be contiguous")
+    esz = t.element_size() if hasattr(t, "element_size") else None
+    if esz is not None and esz != _ELEMENT_BYTES[code]:
+        raise FtlmError(1, f"{name}: elements of {esz} bytes do not match dtype {dtype!r} "
+                           f"({_ELEMENT_BYTES[code]} bytes)")
+    n = t.numel() if hasattr(t, "numel") else None
+    if n is not None and n < int(dim) * int(nvec):
+        raise FtlmError(1, f"{name}: {n} elements, {int(dim) * int(nvec)} needed ([{dim}][{nvec}])")
+
+
+def _check_device(sys, *blocks):
+    """The tensors must live on the current CUDA device (the one the library
+    enqueues on); raises FtlmError otherwise."""
+    for t in blocks:
+        dev = getattr(t, "device", None)
+        if dev is None or getattr(dev, "index", None) is None:
+            continue
+        import torch
+        if dev.index != torch.cuda.current_device():
+            raise FtlmError(1, f"block on {dev}, current device is cuda:{torch.cuda.current_device()}")
+
+
 def _pd(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
@@ -217,13 +257,21 @@ class System:
             pass
 
 
+def _blocks(sys, nvec, dtype, **blocks):
+    for name, t in blocks.items():
+        _check_block(t, sys.dim, nvec, dtype, name)
+    _check_device(sys, *blocks.values())
+
+
 def apply_h(sys: System, x, y, nvec: int, dtype="c64", stream=None):
     """y = H x on device blocks [dim][nvec] (``ftlm_apply_h``)."""
+    _blocks(sys, nvec, dtype, x=x, y=y)
     _check(lib().ftlm_apply_h(sys.handle, _ptr(x), _ptr(y), int(nvec), _DTYPES[dtype], _stream(stream, x, y)))
 
 
 def apply_sdir(sys: System, x, y, nvec: int, dtype="c64", u=None, stream=None):
     """y = (u.S) x (``ftlm_apply_sdir``); u = None uses the field direction."""
+    _blocks(sys, nvec, dtype, x=x, y=y)
     uu = _f64(u)
     _check(lib().ftlm_apply_sdir(sys.handle, _pd(uu), _ptr(x), _ptr(y), int(nvec), _DTYPES[dtype],
                                  _stream(stream, x, y)))
@@ -231,18 +279,21 @@ def apply_sdir(sys: System, x, y, nvec: int, dtype="c64", u=None, stream=None):
 
 def start_block(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dtype="c64", stream=None):
     """Normalised Gaussian start vectors into a device block (``ftlm_start_block``)."""
+    _blocks(sys, nvec, dtype, out=out)
     _check(lib().ftlm_start_block(sys.handle, int(seed), int(vec_offset), _ptr(out), int(nvec), _DTYPES[dtype],
                                   _stream(stream, out)))
 
 
 def start_pairs(sys: System, out, nvec: int, seed: int, vec_offset: int = 0, dtype="c64", stream=None):
     """Normalised pairs of time-reversed random vectors (``ftlm_start_pairs``)."""
+    _blocks(sys, nvec, dtype, out=out)
     _check(lib().ftlm_start_pairs(sys.handle, int(seed), int(vec_offset), _ptr(out), int(nvec), _DTYPES[dtype],
                                   _stream(stream, out)))
 
 
 def time_reverse(sys: System, x, y, nvec: int, dtype="c64", stream=None):
     """y = Theta x, Theta = exp(-i pi S^y) K (``ftlm_time_reverse``)."""
+    _blocks(sys, nvec, dtype, x=x, y=y)
     _check(lib().ftlm_time_reverse(sys.handle, _ptr(x), _ptr(y), int(nvec), _DTYPES[dtype], _stream(stream, x)))
 
 
@@ -251,12 +302,13 @@ def start_block_noalloc(sys: System, out, nvec: int, seed: int, vec_offset: int 
     may not allocate (``ftlm_start_block_noalloc``): its scratch is a static
     device array inside the library, so at most 64 vectors, and calls that
     overlap on the GPU race on that array."""
+    _blocks(sys, nvec, dtype, out=out)
     _check(lib().ftlm_start_block_noalloc(sys.handle, int(seed), int(vec_offset), _ptr(out), int(nvec),
                                           _DTYPES[dtype], _stream(stream, out)))
 
 
 def _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, obs_dir, breakdown_tol, autotune,
-            time_kernels, stream, keep, symmetric=False):
+            time_kernels, stream, keep, symmetric=False, reorth=False):
     T = _f64(T)
     od = _f64(obs_dir)
     keep += [T, od]
@@ -265,7 +317,7 @@ def _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, o
         else int(start)
     return RunParams(int(R), int(M), int(seed), int(vec_offset), _DTYPES[dtype], mode, int(basis_offset),
                      _ptr(user_start), _pd(T), len(T), _pd(od), float(breakdown_tol), int(autotune),
-                     int(time_kernels), _stream(stream, user_start), int(bool(symmetric)))
+                     int(time_kernels), _stream(stream, user_start), int(bool(symmetric)), int(bool(reorth)))
 
 
 def _result(R, M, nT, keep, symmetric=False):
@@ -297,26 +349,30 @@ def _finish(r, out):
 
 def run(sys: System, R: int, M: int, T, seed: int = 0, vec_offset: int = 0, dtype="c64", start="random",
         basis_offset: int = 0, user_start=None, obs_dir=None, breakdown_tol: float = 0.0, autotune=False,
-        time_kernels=False, stream=None, symmetric=False) -> dict:
+        time_kernels=False, stream=None, symmetric=False, reorth=False) -> dict:
     """FTLM (``ftlm_run``): returns lnZ, E, C, M_B, M_B_imag per T, E0, and the
     per-vector alpha, beta, p, M_eff; with symmetric=True also the symmetric
     estimator M_B_sym, M_B_sym_imag (Eqs. E-2-G, E-2-H), the matrices
-    O[r, i, j] = <v_i|u.S|v_j> and sym_ms."""
+    O[r, i, j] = <v_i|u.S|v_j> and sym_ms; reorth=True re-orthogonalises every
+    new Lanczos vector against all previous ones of its chain."""
     keep = []
+    if user_start is not None:
+        _check_block(user_start, sys.dim, R, dtype, "user_start")
     p = _params(R, M, T, seed, vec_offset, dtype, start, basis_offset, user_start, obs_dir, breakdown_tol, autotune,
-                time_kernels, stream, keep, symmetric)
+                time_kernels, stream, keep, symmetric, reorth)
     r, out = _result(R, M, p.nT, keep, symmetric)
     _check(lib().ftlm_run(sys.handle, ctypes.byref(p), ctypes.byref(r)))
     return _finish(r, out)
 
 
 def run_batch(systems, R: int, M: int, T, seed: int = 0, vec_offset: int = 0, dtype="c64", obs_dir=None,
-              breakdown_tol: float = 0.0, autotune=False, time_kernels=False, stream=None, start="random") -> list:
+              breakdown_tol: float = 0.0, autotune=False, time_kernels=False, stream=None, start="random",
+              reorth=False) -> list:
     """FTLM for several systems in one graph (``ftlm_run_batch``); start is
-    "random", "pairs" or "basis"."""
+    "random", "pairs" or "basis" (reorth=True is rejected: one system only)."""
     keep = []
     p = _params(R, M, T, seed, vec_offset, dtype, start, 0, None, obs_dir, breakdown_tol, autotune, time_kernels,
-                stream, keep)
+                stream, keep, reorth=reorth)
     n = len(systems)
     rs, outs = [], []
     for _ in range(n):
@@ -356,10 +412,13 @@ class CsrMatrix:
         _check(lib().ftlm_csr_create(sys.handle, _DTYPES[dtype], ctypes.byref(h)))
         self.handle = h.value
         self.dtype = dtype
+        self.dim = sys.dim
         self.nnz = int(lib().ftlm_csr_nnz(self.handle))
         self.bytes = int(lib().ftlm_csr_bytes(self.handle))
 
     def apply(self, x, y, nvec: int, stream=None):
+        for name, t in (("x", x), ("y", y)):
+            _check_block(t, self.dim, nvec, self.dtype, name)
         _check(lib().ftlm_csr_apply(self.handle, _ptr(x), _ptr(y), int(nvec), _stream(stream, x)))
 
     def close(self):

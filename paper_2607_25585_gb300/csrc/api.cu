@@ -85,6 +85,7 @@ struct ftlm_system {
   DevBuf Hq;             // H q_j when the gather and the step epilogue are separate launches
   DevBuf ep, ecnt, esc;  // start-block scratch: partials, arrival counter, scalars
   DevBuf Vs, Wc, Od;     // symmetric runs: stored Lanczos vectors, u.S chunk, O matrices
+  DevBuf Gre;            // re-orthogonalised runs: <q_k|w_r> coefficients [R][M] complex
   std::mutex mu;
 };
 
@@ -555,6 +556,7 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
            pl.grid, p->breakdown_tol, u[0], u[1], u[2], p->obs_dir ? 1 : 0, p->stream);
   k += buf;
   k += p->symmetric ? "|sym" : "";
+  k += p->reorth ? "|reorth" : "";
   snprintf(buf, sizeof buf, "|half%d vm%d hy%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
            pl.half.hybrid ? 1 : 0,
            pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
@@ -579,6 +581,9 @@ ftlm_status validate_params(const ftlm_run_params* p, const std::vector<ftlm_sys
     return fail(FTLM_ERR_INVALID_ARG, "user start vectors need a single system");
   if (p->symmetric && sys.size() != 1) return fail(FTLM_ERR_INVALID_ARG, "symmetric runs take one system");
   if (p->symmetric != 0 && p->symmetric != 1) return fail(FTLM_ERR_INVALID_ARG, "symmetric must be 0 or 1");
+  if (p->reorth != 0 && p->reorth != 1) return fail(FTLM_ERR_INVALID_ARG, "reorth must be 0 or 1");
+  if (p->reorth && sys.size() != 1)
+    return fail(FTLM_ERR_UNSUPPORTED, "re-orthogonalised runs take one system (ftlm_run)");
   if (!(p->breakdown_tol >= 0) || !std::isfinite(p->breakdown_tol))
     return fail(FTLM_ERR_INVALID_ARG, "breakdown_tol must be finite and >= 0");
   if (p->obs_dir && !(std::isfinite(p->obs_dir[0]) && std::isfinite(p->obs_dir[1]) && std::isfinite(p->obs_dir[2])))
@@ -650,7 +655,8 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
     a.inst = (j % 2 == 0) ? d_even : d_odd;
     a.step = j;
     a.first = j == 0;
-    if (p->symmetric) {  // keep q_j (vector-major) for the matrix of u.S in the Lanczos basis
+    if (p->symmetric || p->reorth) {  // keep q_j (vector-major): the matrix of u.S in the Lanczos basis, or
+                                       // the vectors the next ones are re-orthogonalised against
       ftlm_system* s0 = sys[0];
       const size_t vb = (size_t)s0->hs.dim * R * (c64 ? 8 : 16);
       const void* q = (j % 2 == 0) ? s0->A.p : s0->B.p;
@@ -690,6 +696,19 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
     CKI(launch_plan(pl, a, st));
     ctx.launches += 2;
     ctx.hv_launches++;
+    if (p->reorth) {  // two Gram-Schmidt passes against q_0..q_j, then the norm of what is left
+      ftlm_system* s0 = sys[0];
+      const DevScalars sc = scalars_at(s0->scal.p, R, M);
+      void* w = (j % 2 == 0) ? s0->B.p : s0->A.p;
+      for (int pass = 0; pass < 2; ++pass)
+        CKI(launch_reorth_pass(s0->Vs.p, w, (long long)s0->hs.dim, R, j, M, reinterpret_cast<double*>(s0->Gre.p),
+                               sc.sigma, c64, st));
+      a.mode = kModeUpdate;
+      a.update_no_alpha = 1;
+      CKI(launch_plan(pl, a, st));
+      a.update_no_alpha = 0;
+      ctx.launches += 5;
+    }
   }
   if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
   const size_t per = staged_bytes(R, M);
@@ -886,7 +905,15 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     if (w != FTLM_OK) return w;
   }
   Plan pl;
-  ftlm_status ps = make_plan(sys, R, c64, pl, nullptr, true);
+  ftlm_status ps;
+  if (p->reorth) {  // the general row kernel on the row-major block, gather and update in two launches
+    Shape gen = default_shape(R, c64);
+    gen.explicit_general = true;
+    ps = make_plan(sys, R, c64, pl, &gen, false);
+    pl.wideV = 0;
+  } else {
+    ps = make_plan(sys, R, c64, pl, nullptr, true);
+  }
   if (ps != FTLM_OK) return ps;
   if (pl.half.on) {
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
@@ -897,13 +924,23 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
       if (hs_ != FTLM_OK) return hs_;
     }
   }
-  if (p->symmetric) {  // the M Lanczos vectors of every vector
+  if (p->symmetric || p->reorth) {  // the M Lanczos vectors of every vector
     ftlm_system* s0 = sys[0];
     const size_t vb = (size_t)s0->hs.dim * R * (c64 ? 8 : 16) * M;
     if (s0->Vs.bytes < vb) {
       s0->Vs.release();
       if (s0->Vs.ensure(vb) != cudaSuccess)
-        return fail(FTLM_ERR_OUT_OF_MEMORY, "symmetric run: " + std::to_string(vb) + " bytes of Lanczos vectors");
+        return fail(FTLM_ERR_OUT_OF_MEMORY, std::string(p->symmetric ? "symmetric" : "re-orthogonalised") +
+                                                " run: " + std::to_string(vb) + " bytes of Lanczos vectors");
+      s0->gen++;
+    }
+  }
+  if (p->reorth) {
+    ftlm_system* s0 = sys[0];
+    const size_t gb = sizeof(double) * 2 * (size_t)R * M;
+    if (s0->Gre.bytes < gb) {
+      s0->Gre.release();
+      CK(s0->Gre.ensure(gb));
       s0->gen++;
     }
   }
@@ -1121,9 +1158,23 @@ ftlm_status check_block_args(const ftlm_system* s, const void* x, const void* y,
   return FTLM_OK;
 }
 
+// The coupling tables and the workspace of a system live on the device that
+// was current when it was created; work for it must be enqueued with that
+// device current (pointers of one device are not valid on another).
+ftlm_status check_device(const ftlm_system* s) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev != s->device)
+    return fail(FTLM_ERR_INVALID_ARG, "system lives on device " + std::to_string(s->device) + ", current device is " +
+                                          std::to_string(dev));
+  return FTLM_OK;
+}
+
 ftlm_status rows_entry(const ftlm_system* cs, int mode, const double* u, const void* x, void* y, int nvec,
                        ftlm_dtype dtype, void* stream) {
   ftlm_status v = check_block_args(cs, x, y, nvec, dtype);
+  if (v != FTLM_OK) return v;
+  v = check_device(cs);
   if (v != FTLM_OK) return v;
   const int c64 = dtype == FTLM_C64;
   ftlm_system* s = const_cast<ftlm_system*>(cs);
@@ -1185,8 +1236,9 @@ ftlm_status ftlm_start_block_noalloc(const ftlm_system* cs, uint64_t seed, uint6
   const int c64 = dtype == FTLM_C64;
   ftlm_system* s = const_cast<ftlm_system*>(cs);
   std::lock_guard<std::mutex> lk(s->mu);
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+  v = check_device(s);
+  if (v != FTLM_OK) return v;
+  const int dev = s->device;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(FTLM_ERR_UNSUPPORTED, "device ordinal too large");
   void* base = nullptr;
   {
@@ -1279,7 +1331,7 @@ void ftlm_system_destroy(ftlm_system* s) {
   cudaDeviceSynchronize();  // the system's buffers may be in use on any stream
   purge_ctx_of(s->id);
   for (DevBuf* b : {&s->tab_f, &s->tab_d, &s->stride, &s->q, &s->A, &s->B, &s->U, &s->scal, &s->ep, &s->ecnt,
-                    &s->esc, &s->Hq})
+                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre})
     b->release();
   cudaEventDestroy(s->ev_in);
   cudaEventDestroy(s->ev_out);
@@ -1318,6 +1370,8 @@ ftlm_status start_block_impl(const ftlm_system* cs, uint64_t seed, uint64_t vec_
   const int c64 = dtype == FTLM_C64;
   ftlm_system* s = const_cast<ftlm_system*>(cs);
   std::lock_guard<std::mutex> lk(s->mu);
+  v = check_device(s);
+  if (v != FTLM_OK) return v;
   cudaStream_t st = pick_stream(s, stream);
   Plan pl;
   std::vector<ftlm_system*> one{s};
@@ -1372,17 +1426,22 @@ ftlm_status ftlm_time_reverse(const ftlm_system* cs, const void* x, void* y, int
   const size_t bytes = (size_t)cs->hs.dim * nvec * (c64 ? 8 : 16);
   const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
   if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
+  v = check_device(cs);
+  if (v != FTLM_OK) return v;
   InstDesc h = base_desc(cs, c64);
   CKI(launch_time_reverse(&h, x, y, nvec, c64, pick_stream(cs, stream)));
   return FTLM_OK;
 }
 
 ftlm_status ftlm_run(const ftlm_system* s, const ftlm_run_params* p, ftlm_result* res) {
-  if (!s) return fail(FTLM_ERR_INVALID_ARG, "system is NULL");
   ftlm_system* ms = const_cast<ftlm_system*>(s);
+  ftlm_status pv = validate_params(p, {ms});  // host-only: before any lock or CUDA call
+  if (pv != FTLM_OK) return pv;
   std::lock_guard<std::mutex> lk(ms->mu);
   if (p && p->autotune) {
     ftlm_status vs = validate_params(p, {ms});
+    if (vs != FTLM_OK) return vs;
+    vs = check_device(ms);
     if (vs != FTLM_OK) return vs;
     ftlm_status a = autotune(ms, p->R, p->dtype == FTLM_C64, pick_stream(ms, p->stream));
     if (a != FTLM_OK) return a;
@@ -1407,6 +1466,10 @@ ftlm_status ftlm_run_batch(int n, const ftlm_system* const* systems, const ftlm_
   if (p && p->autotune) {
     ftlm_status vs = validate_params(p, v);
     if (vs != FTLM_OK) return vs;
+    for (auto* s : v) {
+      vs = check_device(s);
+      if (vs != FTLM_OK) return vs;
+    }
     ftlm_system* big = v[0];
     for (auto* s : v)
       if (s->hs.dim > big->hs.dim) big = s;
@@ -1535,6 +1598,9 @@ ftlm_status ftlm_csr_apply(const ftlm_csr* m, const void* x, void* y, int nvec, 
   const size_t bytes = (size_t)m->dim * nvec * (m->c64 ? 8 : 16);
   const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
   if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(FTLM_ERR_INVALID_ARG, "matrix lives on another device");
   CKI(launch_csr_spmm(m->dim, nvec, reinterpret_cast<const long long*>(m->rp.p), reinterpret_cast<const int*>(m->col.p),
                       m->val.p, x, y, m->c64, reinterpret_cast<cudaStream_t>(stream)));
   return FTLM_OK;

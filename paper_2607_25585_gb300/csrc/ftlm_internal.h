@@ -157,6 +157,9 @@ struct LaunchArgs {
   // kModeStep / kModeEpilogue: H q_j = sum of hq_parts blocks hq + p * hq_stride
   int hq_parts = 1;
   long long hq_stride = 0;
+  // kModeUpdate: 1 = leave w as it is (no alpha term) and only take its norm,
+  // beta and sigma (after a re-orthogonalisation)
+  int update_no_alpha = 0;
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -218,6 +221,12 @@ int vm_max_ctas_per_sm(int K, int min_blocks, int c64, int threads, size_t smem,
 // kModeStep / kModeStartNorm over the same one-vector instances (256 threads)
 int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream);
 constexpr int kVmLaneBits = 5;  // rows per warp-wide load: 2^5
+
+// Full re-orthogonalisation pass (reorth.cu): w_r -= sum_{k<=j} sigma_k^2 <q_k|w_r> q_k
+// for the R vectors of a row-major block w [dim][R], against the stored
+// vector-major q_k (Vs [M][R][dim]); G is [R][M] complex FP64 scratch, sigma [M+1][R].
+int launch_reorth_pass(const void* Vs, void* w, long long dim, int R, int j, int M, double* G, const double* sigma,
+                       int c64, void* stream);
 
 // Stored-matrix comparison path (csr.cu): count, scan, fill, multiply.
 size_t csr_smem_bytes(const LaunchArgs& a, int c64);

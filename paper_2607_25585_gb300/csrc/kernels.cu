@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
           if (MODE == kModeStep)
             coef[v] = (real)(d.sc.alpha[(size_t)j * d.sc.ss + k] * d.sc.sigma[(size_t)j * d.sc.ss + k]);
         } else if (MODE == kModeUpdate) {
-          coef[v] = (real)(d.sc.alpha[(size_t)j * d.sc.ss + k] * d.sc.sigma[(size_t)j * d.sc.ss + k]);
+          coef[v] = a.update_no_alpha ? (real)0
+                                      : (real)(d.sc.alpha[(size_t)j * d.sc.ss + k] * d.sc.sigma[(size_t)j * d.sc.ss + k]);
         } else if (MODE == kModeApplyS) {
           coef[v] = a.use_sigma0 ? (real)d.sc.sigma[k] : (real)1;
         } else if (MODE == kModeScale) {

@@ -38,6 +38,91 @@ def test_version():
     assert "sm_103a" in F.version()
 
 
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes structures of the binding have the field offsets and sizes
+    that a C compiler gives the structs of include/ftlm.h (a plain C program
+    built with gcc prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ftlm_run_params": F.RunParams, "ftlm_result": F.Result, "ftlm_constants": F.Constants}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ftlm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for ln in out:
+        if not ln.strip():
+            continue
+        cname, field, val = ln.split()
+        py = structs[cname]
+        expect = ctypes.sizeof(py) if field == "sizeof" else getattr(py, field).offset
+        assert int(val) == expect, (cname, field)
+        seen += 1
+    assert seen == sum(len(p._fields_) + 1 for p in structs.values())
+
+
+def test_run_params_reorth_validated_on_host():
+    """ftlm_run_params.reorth takes 0 (the three-term recurrence) or 1 (full
+    re-orthogonalisation); anything else is rejected before the library
+    looks at the system or touches the GPU."""
+    import ctypes
+    keep = []
+    T = W.temperatures()
+    p = F._params(2, 5, T, 0, 0, "c64", "random", 0, None, None, 0.0, False, False, None, keep)
+    r, _ = F._result(2, 5, len(T), keep)
+    for bad in (2, -1):
+        p.reorth = bad
+        assert F.lib().ftlm_run(None, ctypes.byref(p), ctypes.byref(r)) == 1
+        assert "reorth" in F.lib().ftlm_last_error().decode()
+    p.reorth = 1
+    assert F.lib().ftlm_run(None, ctypes.byref(p), ctypes.byref(r)) == 1
+    assert "system is NULL" in F.lib().ftlm_last_error().decode()
+
+
+def test_binding_checks_blocks_before_the_library():
+    """The Python binding refuses a tensor block that is not on a CUDA device,
+    not contiguous, of the wrong element size for the dtype, or too small for
+    [dim][nvec], before any pointer reaches the library (no GPU needed: the
+    checks run on CPU tensors)."""
+    torch = pytest.importorskip("torch")
+    ok = torch.zeros(8, 4, dtype=torch.complex64)
+    with pytest.raises(F.FtlmError, match="device block"):
+        F._check_block(ok, 8, 4, "c64")
+
+    class Fake:  # a device tensor stand-in: only the attributes the check reads
+        def __init__(self, t, dev="cuda"):
+            self.t, self.device = t, torch.device(dev)
+
+        def is_contiguous(self):
+            return self.t.is_contiguous()
+
+        def element_size(self):
+            return self.t.element_size()
+
+        def numel(self):
+            return self.t.numel()
+
+    F._check_block(Fake(ok), 8, 4, "c64")
+    F._check_block(12345, 8, 4, "c64")                  # raw pointers pass through
+    with pytest.raises(F.FtlmError, match="do not match"):
+        F._check_block(Fake(ok), 8, 4, "c128")           # complex64 storage passed as complex128
+    with pytest.raises(F.FtlmError, match="elements"):
+        F._check_block(Fake(ok), 8, 5, "c64")            # too small for [8][5]
+    with pytest.raises(F.FtlmError, match="contiguous"):
+        F._check_block(Fake(torch.zeros(4, 8, dtype=torch.complex64).t()), 8, 4, "c64")
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(two_s=[1, 0]), "two_s"),
     (dict(two_s=[1, 16]), "two_s"),

@@ -52,6 +52,29 @@ def test_apply_h_matches_oracle(name, dtype, R, rng):
     assert rel_l2(y, ref) < TOL[dtype]
 
 
+@pytest.mark.parametrize("name", sorted(SYSTEMS))
+def test_apply_h_c64_per_row_bound(name, rng):
+    """complex64, row by row: |y_mu - (Hx)_mu| <= 1e-5 * sum_nu |H_mu,nu| |x_nu|.
+    The bound is what FP32 products and sums can lose (coefficients rounded
+    to FP32, ~K u relative to the sum of absolute terms for K terms), so a
+    wrong or missing term in any single row fails it even when the block-wide
+    relative L2 would hide it."""
+    from oracle import dense
+    w = SYSTEMS[name](rng)
+    s = F.System.from_dict(w)
+    d, R = s.dim, 8
+    x = rng.normal(size=(d, R)) + 1j * rng.normal(size=(d, R))
+    x = x.astype(np.complex64).astype(np.complex128)
+    H = dense.hamiltonian(osys(w))
+    ref = H @ x
+    bound = np.abs(H) @ np.abs(x)
+    yd = empty_dev((d, R), "c64")
+    F.apply_h(s, to_dev(x, "c64"), yd, R, "c64")
+    err = np.abs(yd.cpu().numpy() - ref)
+    assert np.all(bound > 0)
+    assert np.max(err / bound) < 1e-5
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("shape", [(0, 1, 2), (2, 1, 1), (2, 5, 4), (3, 10, 2), (4, 2, 1), (4, 10, 8), (3, 3, 2),
                                    (2, 1, 1, 1), (3, 10, 2, 1), (3, 3, 4, 1), (4, 5, 4, 1), (4, 10, 8, 1),

@@ -89,6 +89,64 @@ def test_exact_mode_all_basis_vectors_equals_ed(two_s, rng):
     assert np.abs(r["M_B_imag"]).max() < 1e-10 * np.abs(ex["M_B"]).max()
 
 
+@pytest.mark.slow
+def test_exact_mode_on_the_s1_ring_equals_ed():
+    """The same at d = 243: a ring of five s = 1 sites with every term of
+    Eq. (3) (the model of the N = 6 ring, one site fewer).  243 start vectors
+    x 243 steps with full re-orthogonalisation and 243 Jacobi eigensolves of
+    order 243 (about 20 s on eight host threads).  The N = 6 ring itself
+    (d = 729) costs about 40 s per Jacobi eigensolve, i.e. hours for the 729
+    start vectors; it is checked by the next test."""
+    s = oracle_system(W.ring(N=5, two_s=2))
+    d = s.dim
+    r = oracle.ftlm(s, R=d, M=d, T=T, start="basis", reorth=True)
+    ex = dense.thermo_exact(s, T)
+    for k in ("lnZ", "E", "C", "M_B"):
+        assert _rel(r[k], ex[k], 1e-6) < 1e-10, k
+
+
+@pytest.mark.slow
+def test_ring6_all_basis_vectors_full_depth_equals_ed():
+    """The N = 6, s = 1 ring (d = 729, tilted axes, oblique field, dipolar
+    coupling): the oracle's three-term recurrence (no re-orthogonalisation,
+    as on the hot path) from each of the 729 basis vectors, 729 steps deep.
+    With the Krylov space complete, Eqs. (4)-(5) over all basis vectors are
+    the exact traces Tr(e^{-H/T}), Tr(H e^{-H/T}), Tr(u.S e^{-H/T}); the
+    eigenpairs of each tridiagonal matrix come from LAPACK's tridiagonal
+    solver here, since the oracle's Jacobi takes about 40 s at order 729.
+    Against exact diagonalisation of the dense Hamiltonian, within 1e-10
+    (about 90 s on eight host threads).  d = 4096 would cost
+    (4096/729)^3 = 177 times the recurrence work: out of reach on the CPU."""
+    from scipy.linalg import eigh_tridiagonal
+    w = W.ring6_s1()
+    s = oracle_system(w)
+    d = s.dim
+    r = oracle.ftlm_tridiag(s, R=d, M=d, start="basis")
+    assert np.all(r["M_eff"] == d)                      # every Krylov space is the whole space
+    ev_all, u0_all, q_all = [], [], []
+    for k in range(d):
+        ev, U = eigh_tridiagonal(r["alpha"][k], r["beta"][k, : d - 1])
+        ev_all.append(ev)
+        u0_all.append(U[0])
+        q_all.append(U.T @ np.conj(r["p"][k]))          # <r|u.S|n> = sum_j U_jn conj(p_j)
+    ev, u0, q = np.array(ev_all), np.array(u0_all), np.array(q_all)
+    E0 = ev.min()
+    g = float(w["g"])
+    res = {k: np.empty(len(T)) for k in ("lnZ", "E", "C", "M_B")}
+    for t, Tk in enumerate(T):                           # Eqs. (4), (5) with R = d, prefactor d / R = 1
+        bz = np.exp(-(ev - E0) / Tk)
+        wgt = u0 ** 2 * bz
+        z = wgt.sum()
+        Em = (wgt * ev).sum() / z
+        res["lnZ"][t] = np.log(z) - E0 / Tk
+        res["E"][t] = Em
+        res["C"][t] = (wgt * (ev - Em) ** 2).sum() / z / Tk ** 2
+        res["M_B"][t] = -g * (bz * u0 * q).sum().real / z
+    ex = dense.thermo_exact(s, T)
+    for k in res:
+        assert _rel(res[k], ex[k], 1e-6) < 1e-10, k
+
+
 def test_exact_krylov_random_vectors_equals_trace_estimate(rng):
     """With the Krylov space complete, the FTLM estimate for fixed random
     vectors equals the exact stochastic trace sum_r <r|f(H)|r> (Eqs. 1, 4, 5)."""

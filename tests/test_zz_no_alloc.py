@@ -40,6 +40,30 @@ def test_no_alloc_start_block_matches_the_allocating_one():
                 assert np.allclose(np.linalg.norm(g, axis=0), 1.0, atol=1e-6 if dtype == "c64" else 1e-14)
 
 
+def test_no_alloc_full_size_more_ctas_than_its_scratch_holds():
+    """d = 1,048,576 x 64 vectors: the allocating call launches more CTAs than
+    the static scratch has partial-sum slots (256), so the allocation-free
+    call runs on fewer CTAs and sums the norms over another partition; the
+    blocks agree within the tolerance of the start-block tests and every
+    column has norm 1."""
+    s = F.System.from_dict(W.lattice4x5())
+    d, R = s.dim, 64
+    for call in range(2):
+        for dtype in ("c128", "c64"):
+            ref = empty_dev((d, R), dtype)
+            F.start_block(s, ref, R, seed=7, vec_offset=call, dtype=dtype)
+            got = empty_dev((d, R), dtype)
+            got.zero_()
+            F.start_block_noalloc(s, got, R, seed=7, vec_offset=call, dtype=dtype)
+            torch = torch_cuda()
+            diff = torch.linalg.vector_norm((got - ref).to(torch.complex128)).item()
+            nref = torch.linalg.vector_norm(ref.to(torch.complex128)).item()
+            assert diff / nref < TOL[dtype], (call, dtype)
+            norms = torch.linalg.vector_norm(got.to(torch.complex128), dim=0).cpu().numpy()
+            assert np.allclose(norms, 1.0, atol=1e-6 if dtype == "c64" else 1e-14)
+            del ref, got
+
+
 def test_no_alloc_rejects_blocks_beyond_its_scratch():
     s = F.System.from_dict(W.square_lattice(4, 3, seed=1))
     out = empty_dev((s.dim, 65), "c64")
