@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libftlm_gb300.so")
-SOURCES = ["kernels.cu", "hv_half.cu", "hv_vm.cu", "csr.cu", "reorth.cu", "api.cu", "tables.cpp", "tridiag.cpp"]
+SOURCES = ["kernels.cu", "hv_half.cu", "hv_vm.cu", "csr.cu", "reorth.cu", "sym.cu", "api.cu", "tables.cpp", "tridiag.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp, "-lcublas", "-lpthread",
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp, "-lpthread",
            "-Xlinker", f"-rpath,{cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -2,7 +2,6 @@
 // and start-block entry points, and the FTLM driver (arxiv 2607.25585,
 // Eqs. 4-5 and Sec. II.C): start block, M Lanczos steps captured in one CUDA
 // graph, then the host eigensolve and Boltzmann sums.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -792,73 +791,36 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
 
 // ---- symmetric estimator: O_ij = <v_i|u.S|v_j> per vector ---------------------
 
-std::mutex g_blas_mu;
-cublasHandle_t g_blas[64] = {};  // one cuBLAS handle per device, created on first use
-
-cublasHandle_t blas_handle() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lk(g_blas_mu);
-  if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
-  return g_blas[dev];
-}
-
-// After a symmetric run: G_r = Q_r^H (u.S Q_r) for the stored unnormalised
-// vectors Q_r = [q_0 .. q_{M-1}] of every vector r, row chunk by row chunk (the
-// u.S kernel writes a chunk of u.S Q, a strided-batched complex GEMM adds its
-// share to G_r), then O_ij = sigma_i sigma_j G_ij on the host.  Omat [R][M][M]
-// complex row-major; sigma [M][R].
+// After a symmetric run: G_r[i][j] = <q_i|u.S q_j> for the stored unnormalised
+// vectors q_0 .. q_{M-1} of every vector r, in one fused kernel (u.S q_j is
+// formed tile by tile in shared memory, never stored) plus a fixed-order
+// reduction of its per-range partials; then O_ij = sigma_i sigma_j G_ij on
+// the host.  Omat [R][M][M] complex row-major; sigma [M][R].
 ftlm_status symmetric_matrices(ftlm_system* s, const ftlm_run_params* p, cudaStream_t st, const double* sigma,
                                std::vector<double>& Omat, double& ms) {
   const int R = p->R, M = p->M, c64 = p->dtype == FTLM_C64;
   const long long d = (long long)s->hs.dim;
-  const size_t esz = c64 ? 8 : 16;
-  const long long nv = (long long)M * R;
-  if ((long long)R * d >= (1ll << 31)) return fail(FTLM_ERR_UNSUPPORTED, "R * dim must be below 2^31 for symmetric runs");
-  long long rows = std::max<long long>(256, (256ll << 20) / (nv * (long long)esz));
-  rows = std::min<long long>(rows, d);
-  if (s->Wc.bytes < (size_t)(nv * rows) * esz) {
+  const int nranges = sym_ranges(d, R, M);
+  const size_t pbytes = sizeof(double) * sym_partial_doubles(R, M, nranges);
+  if (s->Wc.bytes < pbytes) {
     s->Wc.release();
-    if (s->Wc.ensure((size_t)(nv * rows) * esz) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "u.S chunk");
+    if (s->Wc.ensure(pbytes) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "O matrix partial sums");
   }
-  const size_t obytes = (size_t)R * M * M * esz;
+  const size_t obytes = sizeof(double) * 2 * (size_t)R * M * M;
   if (s->Od.bytes < obytes) {
     s->Od.release();
     if (s->Od.ensure(obytes) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "O matrices");
   }
-  cublasHandle_t h = blas_handle();
-  if (!h) return fail(FTLM_ERR_CUDA, "cuBLAS handle");
-  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(FTLM_ERR_CUDA, "cublasSetStream");
   InstDesc hd = base_desc(s, c64);
   observable_coefs(s->hs, p->obs_dir, hd.obs);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, st));
-  for (long long c0 = 0; c0 < d; c0 += rows) {
-    const int cnt = (int)std::min<long long>(rows, d - c0);
-    CKI(launch_sdir_vm(&hd, s->Vs.p, s->Wc.p, (int)nv, c0, cnt, (int)rows, c64, st));
-    // G_r (M x M, column-major) (+)= A_r^H B_r with A_r = Q_r[c0 : c0 + cnt, :] (column j
-    // at Vs + (j R + r) d + c0, so lda = R d, batch stride d) and B_r the chunk of u.S Q_r
-    // (column j at Wc + (j R + r) rows, ldb = R rows, batch stride rows)
-    cublasStatus_t bs;
-    if (c64) {
-      const cuComplex one = make_cuComplex(1.f, 0.f), beta = make_cuComplex(c0 == 0 ? 0.f : 1.f, 0.f);
-      bs = cublasCgemmStridedBatched(h, CUBLAS_OP_C, CUBLAS_OP_N, M, M, cnt, &one,
-                                     reinterpret_cast<const cuComplex*>(s->Vs.p) + c0, (int)(R * d), d,
-                                     reinterpret_cast<const cuComplex*>(s->Wc.p), (int)(R * rows), rows, &beta,
-                                     reinterpret_cast<cuComplex*>(s->Od.p), M, (long long)M * M, R);
-    } else {
-      const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), beta = make_cuDoubleComplex(c0 == 0 ? 0.0 : 1.0, 0.0);
-      bs = cublasZgemmStridedBatched(h, CUBLAS_OP_C, CUBLAS_OP_N, M, M, cnt, &one,
-                                     reinterpret_cast<const cuDoubleComplex*>(s->Vs.p) + c0, (int)(R * d), d,
-                                     reinterpret_cast<const cuDoubleComplex*>(s->Wc.p), (int)(R * rows), rows, &beta,
-                                     reinterpret_cast<cuDoubleComplex*>(s->Od.p), M, (long long)M * M, R);
-    }
-    if (bs != CUBLAS_STATUS_SUCCESS) return fail(FTLM_ERR_CUDA, "cuBLAS batched GEMM failed (" + std::to_string((int)bs) + ")");
-  }
+  CKI(launch_sym_omat(&hd, s->Vs.p, R, M, nranges, reinterpret_cast<double*>(s->Wc.p),
+                      reinterpret_cast<double*>(s->Od.p), c64, st));
   CK(cudaEventRecord(e1, st));
-  std::vector<char> host(obytes);
+  std::vector<double> host((size_t)R * M * M * 2);
   CK(cudaMemcpyAsync(host.data(), s->Od.p, obytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   float fms = 0.f;
@@ -870,20 +832,10 @@ ftlm_status symmetric_matrices(ftlm_system* s, const ftlm_run_params* p, cudaStr
   for (int r = 0; r < R; ++r)
     for (int i = 0; i < M; ++i)
       for (int j = 0; j < M; ++j) {
-        const size_t src = (size_t)r * M * M + (size_t)j * M + i;  // column-major G_r(i, j)
-        double gr, gi;
-        if (c64) {
-          const float* f = reinterpret_cast<const float*>(host.data()) + 2 * src;
-          gr = f[0];
-          gi = f[1];
-        } else {
-          const double* f = reinterpret_cast<const double*>(host.data()) + 2 * src;
-          gr = f[0];
-          gi = f[1];
-        }
+        const size_t e = ((size_t)r * M + i) * M + j;
         const double sc = sigma[(size_t)i * R + r] * sigma[(size_t)j * R + r];
-        Omat[(((size_t)r * M + i) * M + j) * 2] = sc * gr;
-        Omat[(((size_t)r * M + i) * M + j) * 2 + 1] = sc * gi;
+        Omat[2 * e] = sc * host[2 * e];
+        Omat[2 * e + 1] = sc * host[2 * e + 1];
       }
   return FTLM_OK;
 }

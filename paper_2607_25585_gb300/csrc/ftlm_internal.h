@@ -190,9 +190,6 @@ int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int
 int launch_start_pairs(const InstDesc* h, int R, uint64_t seed, uint64_t vec_offset, void* out, int c64,
                        void* stream, int vector_major);
 int launch_time_reverse(const InstDesc* h, const void* x, void* y, int R, int c64, void* stream);
-// W[k][t] = (u.S V_k)[c0 + t], t < cnt, for nv vector-major vectors V_k (h->obs = u)
-int launch_sdir_vm(const InstDesc* h, const void* V, void* W, int nv, long long c0, int cnt, int T, int c64,
-                   void* stream);
 int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream);
 size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads, int Vmax = 0);
 int launch_rows_wide(const LaunchArgs& a, int V, int grid, int threads, size_t smem, void* stream);
@@ -227,6 +224,14 @@ constexpr int kVmLaneBits = 5;  // rows per warp-wide load: 2^5
 // vector-major q_k (Vs [M][R][dim]); G is [R][M] complex FP64 scratch, sigma [M+1][R].
 int launch_reorth_pass(const void* Vs, void* w, long long dim, int R, int j, int M, double* G, const double* sigma,
                        int c64, void* stream);
+
+// Symmetric estimator (sym.cu): G[r][i][j] = <q_i|u.S q_j> over the stored
+// vector-major Lanczos vectors Vs ([M][R][dim]) of every vector r, complex
+// FP64 [R][M][M]; Gp holds sym_partial_doubles(R, M, nranges) doubles.
+int sym_ranges(long long dim, int R, int M);
+size_t sym_partial_doubles(int R, int M, int nranges);
+int launch_sym_omat(const InstDesc* h, const void* Vs, int R, int M, int nranges, double* Gp, double* G, int c64,
+                    void* stream);
 
 // Stored-matrix comparison path (csr.cu): count, scan, fill, multiply.
 size_t csr_smem_bytes(const LaunchArgs& a, int c64);

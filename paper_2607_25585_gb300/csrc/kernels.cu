@@ -429,56 +429,6 @@ __global__ void time_reverse_kernel(long long dim, int R, int n, const int* q, i
   if (it < items) one(it);
 }
 
-// The observable u.S on stored Lanczos vectors, for the symmetric estimator
-// (Eqs. E-2-G, E-2-H): V holds nv vectors of dim values each (vector-major,
-// vector k at V + k * dim); W[k][t] = (u.S V_k)[c0 + t] for t < cnt (W rows of
-// T values).  u.S = u_z S^z + a S^+ + conj(a) S^-, a = (u_x - i u_y) / 2, the
-// same site tables as s_row; obs = (u_z, Re a, Im a).
-template <typename real>
-__global__ void sdir_vm_kernel(InstDesc d, const real* __restrict__ V, real* __restrict__ W, int nv, long long c0,
-                               int cnt, int T) {
-  using v2 = typename Cx<real>::v2;
-  const real* t = reinterpret_cast<const real*>(d.tab);
-  const TabLayout& L = d.lay;
-  const int qm = L.qmax;
-  const real uz = (real)d.obs[0], aur = (real)d.obs[1], aui = (real)d.obs[2];
-  const long long total = (long long)nv * cnt;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / cnt;
-    const int tt = (int)(e - k * cnt);
-    const long long mu = c0 + tt;
-    const v2* x = reinterpret_cast<const v2*>(V) + k * d.dim;
-    real ar = 0, ai = 0, msum = 0;
-    long long rem = mu;
-    for (int i = 0; i < d.n; ++i) {
-      const int qi = __ldg(d.q + i);
-      const long long nq = rem / qi;
-      const int a_i = (int)(rem - nq * qi);
-      rem = nq;
-      msum += t[L.off_m + i * qm + a_i];
-      const long long st = __ldg(d.stride + i);
-      if (a_i >= 1) {  // a S^+: from mu - stride
-        const real c = t[L.off_up1 + i * qm + a_i];
-        const v2 xv = __ldg(x + mu - st);
-        ar += c * (aur * xv.x - aui * xv.y);
-        ai += c * (aur * xv.y + aui * xv.x);
-      }
-      if (a_i + 1 < qi) {  // conj(a) S^-: from mu + stride
-        const real c = t[L.off_dn1 + i * qm + a_i];
-        const v2 xv = __ldg(x + mu + st);
-        ar += c * (aur * xv.x + aui * xv.y);
-        ai += c * (aur * xv.y - aui * xv.x);
-      }
-    }
-    const v2 xv = __ldg(x + mu);
-    v2 o;
-    o.x = ar + uz * msum * xv.x;
-    o.y = ai + uz * msum * xv.y;
-    reinterpret_cast<v2*>(W)[k * T + tt] = o;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -635,15 +585,6 @@ int launch_time_reverse(const InstDesc* h, const void* x, void* y, int R, int c6
     time_reverse_kernel<float, 1><<<grid, 256, 0, st>>>(dim, R, h->n, h->q, h->all_half, (const float*)x, (float*)y);
   else
     time_reverse_kernel<double, 1><<<grid, 256, 0, st>>>(dim, R, h->n, h->q, h->all_half, (const double*)x, (double*)y);
-  return (int)cudaGetLastError();
-}
-
-int launch_sdir_vm(const InstDesc* h, const void* V, void* W, int nv, long long c0, int cnt, int T, int c64,
-                   void* stream) {
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int grid = elementwise_grid((long long)nv * cnt);
-  if (c64) sdir_vm_kernel<float><<<grid, 256, 0, st>>>(*h, (const float*)V, (float*)W, nv, c0, cnt, T);
-  else sdir_vm_kernel<double><<<grid, 256, 0, st>>>(*h, (const double*)V, (double*)W, nv, c0, cnt, T);
   return (int)cudaGetLastError();
 }
 
