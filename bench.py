@@ -278,8 +278,9 @@ def per_t_errors(a, b, T, floor=1e-3):
 
 
 def timed_run(F, s, stream, **kw):
+    """One run timed with CUDA events on its stream (the graph is captured in
+    the same call: tens of ms, against runs of seconds here)."""
     import torch
-    F.run(s, stream=stream, **kw)  # captures the graph
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -294,8 +295,10 @@ def precision_legs(F, T, stream, args, s_head, spec_head, res_head):
     (complex128, the same kernels in double) on the same random vectors,
     per temperature: the 4x5 lattice at its full R = 64, M = 200 (the c64 run
     is the headline's last timed run; the c128 run of the whole block is also
-    the batched-FP64 throughput) and the 2x13 ladder at R = 4, M = 300 (both
-    timed as full runs)."""
+    the batched-FP64 throughput) and the 2x13 ladder at M = 300 (both timed as
+    full runs) with --ladder-precision-R vectors: 4, the workload's R, takes
+    about three minutes in FP64 (bound by the FP64 pipes), so the default
+    compares one vector."""
     out = {}
     R, M = spec_head["R"], args.M or spec_head["M"]
     d = s_head.dim
@@ -307,7 +310,7 @@ def precision_legs(F, T, stream, args, s_head, spec_head, res_head):
     if not args.no_ladder_precision:
         spec = W.WORKLOADS["ladder2x13"]
         s = F.System.from_dict(spec["system"]())
-        R, M = spec["R"], spec["M"]
+        R, M = args.ladder_precision_R, spec["M"]
         d = s.dim
         r64, ms64 = timed_run(F, s, stream, R=R, M=M, T=T, seed=spec["seed"], dtype="c64", time_kernels=True)
         r128, ms128 = timed_run(F, s, stream, R=R, M=M, T=T, seed=spec["seed"], dtype="c128")
@@ -647,6 +650,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 legs")
     ap.add_argument("--no-ladder-precision", action="store_true", help="skip the 2x13 ladder in the FP32-vs-FP64 legs")
+    ap.add_argument("--ladder-precision-R", type=int, default=1,
+                    help="vectors of the 2x13 ladder's FP32-vs-FP64 comparison (the workload's R is 4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and ladder measurements")
     ap.add_argument("--ladder-steps", type=int, default=20)

@@ -85,6 +85,9 @@ struct ftlm_system {
   DevBuf ep, ecnt, esc;  // start-block scratch: partials, arrival counter, scalars
   DevBuf Vs, Wc, Od;     // symmetric runs: stored Lanczos vectors, u.S chunk, O matrices
   DevBuf Gre;            // re-orthogonalised runs: <q_k|w_r> coefficients [R][M] complex
+  DevBuf Ta, Tb;         // ftlm_apply_h on spin-1/2 blocks: x and H x in the vector-major layout
+  cudaEvent_t ev_apply = nullptr;  // recorded after the last use of Ta, Tb
+  bool apply_used = false;
   std::mutex mu;
 };
 
@@ -119,6 +122,13 @@ struct ShapeKey {
   }
 };
 std::map<ShapeKey, Shape> g_shapes;
+
+// a launch shape set by ftlm_tune_shape or the autotuner for this system shape
+bool has_shape_override(const ftlm_system* s, int R, int c64) {
+  ShapeKey key{s->hs.n, s->hs.qmax, R, c64, (long long)s->hs.dim};
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_shapes.count(key) != 0;
+}
 
 Shape shape_for(int R, int c64, int threads_target, int tile_factor) {
   const int V = vchunk(c64, R);
@@ -370,7 +380,8 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.ntiles = pl.half.tiles_per_vg * pl.half.nvg;
     a.real_pm = pl.half.real_pm;
     a.min_blocks = pl.half.min_blocks;
-    a.inline_one = (a.inline_one && pl.half.nvg == 1) ? 1 : 0;  // one vector: the descriptor by value
+    // one vector, or a regular block (vm_stride): the descriptor by value
+    a.inline_one = (a.inline_one && (pl.half.nvg == 1 || a.vm_stride)) ? 1 : 0;
     a.pass_stride = (long long)pl.half.nvg * pl.half.dim;
     if (pl.half.hybrid) {  // two launches: the bottom cube (one-pass kernel), then the top cube adds its terms
       LaunchArgs b = a;
@@ -1135,6 +1146,42 @@ ftlm_status rows_entry(const ftlm_system* cs, int mode, const double* u, const v
   if (xa < ya + bytes && ya < xa + bytes) return fail(FTLM_ERR_INVALID_ARG, "x and y overlap");
   Plan pl;
   std::vector<ftlm_system*> one{s};
+  if (mode == kModeApply && nvec > 1 && !has_shape_override(s, nvec, c64)) {
+    // spin-1/2 blocks on the default plan: transpose to vector-major, the runs'
+    // gather, transpose back
+    Plan vp;
+    ftlm_status ps = make_plan(one, nvec, c64, vp, nullptr, true);
+    if (ps == FTLM_OK && vp.half.on && vp.half.vm && vp.half.passes == 1 && !vp.half.hybrid) {
+      // the system's two transposed blocks are shared by its calls: a call waits
+      // for the previous one's kernels (on whatever stream it ran) before reusing them
+      std::lock_guard<std::mutex> lk(s->mu);
+      const size_t block = (size_t)s->hs.dim * nvec * (c64 ? 8 : 16);
+      if (s->Ta.bytes < block || s->Tb.bytes < block) {
+        if (s->apply_used) CK(cudaEventSynchronize(s->ev_apply));
+        s->Ta.release();
+        s->Tb.release();
+        CK(s->Ta.ensure(block));
+        CK(s->Tb.ensure(block));
+        s->apply_used = false;
+      }
+      cudaStream_t st = pick_stream(s, stream);
+      if (s->apply_used) CK(cudaStreamWaitEvent(st, s->ev_apply, 0));
+      CKI(launch_to_vector_major(x, s->Ta.p, (long long)s->hs.dim, nvec, c64, st));
+      LaunchArgs a = vp.base;
+      a.inline_one = 1;
+      a.one = base_desc(s, c64);
+      a.one.x = s->Ta.p;
+      a.one.y = s->Tb.p;
+      a.vm_stride = (long long)s->hs.dim * (c64 ? 8 : 16);
+      a.mode = kModeApply;
+      a.gather_alpha = 0;
+      CKI(launch_plan(vp, a, st));
+      CKI(launch_from_vector_major(s->Tb.p, y, (long long)s->hs.dim, nvec, c64, st));
+      CK(cudaEventRecord(s->ev_apply, st));
+      s->apply_used = true;
+      return FTLM_OK;
+    }
+  }
   // one vector: the row-major and the vector-major layouts coincide, so H.v may
   // use the vector-major gather
   ftlm_status ps = make_plan(one, nvec, c64, pl, nullptr, mode == kModeApply && nvec == 1);
@@ -1247,6 +1294,7 @@ ftlm_status ftlm_system_create(int n_sites, const int* two_s, const double* J, c
   CK(cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_apply, cudaEventDisableTiming));
   {
     std::lock_guard<std::mutex> lk(g_mu);
     s->id = g_next_id++;
@@ -1270,6 +1318,7 @@ ftlm_status ftlm_system_create(int n_sites, const int* two_s, const double* J, c
     s->q.release();
     cudaEventDestroy(s->ev_in);
     cudaEventDestroy(s->ev_out);
+    cudaEventDestroy(s->ev_apply);
     cudaStreamDestroy(s->own_stream);
     return fail(e == cudaErrorMemoryAllocation ? FTLM_ERR_OUT_OF_MEMORY : FTLM_ERR_CUDA,
                 std::string("uploading the coupling tables: ") + cudaGetErrorString(e));
@@ -1283,10 +1332,11 @@ void ftlm_system_destroy(ftlm_system* s) {
   cudaDeviceSynchronize();  // the system's buffers may be in use on any stream
   purge_ctx_of(s->id);
   for (DevBuf* b : {&s->tab_f, &s->tab_d, &s->stride, &s->q, &s->A, &s->B, &s->U, &s->scal, &s->ep, &s->ecnt,
-                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre})
+                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre, &s->Ta, &s->Tb})
     b->release();
   cudaEventDestroy(s->ev_in);
   cudaEventDestroy(s->ev_out);
+  cudaEventDestroy(s->ev_apply);
   cudaStreamDestroy(s->own_stream);
   delete s;
 }

@@ -160,6 +160,9 @@ struct LaunchArgs {
   // kModeUpdate: 1 = leave w as it is (no alpha term) and only take its norm,
   // beta and sigma (after a re-orthogonalisation)
   int update_no_alpha = 0;
+  // vector-major gather of a regular block (inline_one): vector k's x and y
+  // are one.x and one.y advanced by k * vm_stride bytes
+  long long vm_stride = 0;
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -186,6 +189,8 @@ int launch_start_random(const InstDesc* inst_host, const InstDesc* inst_dev, int
 int launch_start_basis(long long dim, int R, uint64_t basis_offset, void* out, int c64, void* stream,
                        int vector_major = 0);
 int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int c64, void* stream);
+// the inverse: dst[nu * R + k] = src[k * dim + nu]
+int launch_from_vector_major(const void* src, void* dst, long long dim, int R, int c64, void* stream);
 // pairs of time-reversed random vectors (unnormalised) and y = Theta x on [d][R]
 int launch_start_pairs(const InstDesc* h, int R, uint64_t seed, uint64_t vec_offset, void* out, int c64,
                        void* stream, int vector_major);

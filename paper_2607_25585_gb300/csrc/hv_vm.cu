@@ -274,8 +274,13 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
     if (inst != cur) {  // per-vector pointers (the tables are shared)
       if (kPartials && cur >= 0) flush(cur, adot);
       adot = 0.0;
-      x = insts[inst].x;
-      y0 = insts[inst].y;
+      if (a.vm_stride) {  // a regular vector-major block: vector inst at a fixed stride
+        x = static_cast<const char*>(a.one.x) + (long long)inst * a.vm_stride;
+        y0 = static_cast<char*>(a.one.y) + (long long)inst * a.vm_stride;
+      } else {
+        x = insts[inst].x;
+        y0 = insts[inst].y;
+      }
       cur = inst;
     }
     const int s0 = MP ? cube_lo(pass) : CB;                 // cube bits [s0, s0 + K)

@@ -624,6 +624,41 @@ int launch_to_vector_major(const void* src, void* dst, long long dim, int R, int
   return (int)cudaGetLastError();
 }
 
+// dst[nu * R + k] = src[k * dim + nu]: a vector-major block back to the
+// row-major layout, through 32 x 32 shared-memory tiles as above.
+template <typename v2>
+__global__ void from_vector_major_kernel(const v2* __restrict__ src, v2* __restrict__ dst, long long dim, int R) {
+  __shared__ v2 tile[32][33];
+  const long long row_tiles = (dim + 31) / 32;
+  const int vec_tiles = (R + 31) / 32;
+  for (long long t = blockIdx.x; t < row_tiles * vec_tiles; t += gridDim.x) {
+    const long long nu0 = (t / vec_tiles) * 32;
+    const int k0 = (int)(t % vec_tiles) * 32;
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int k = k0 + i;
+      const long long nu = nu0 + threadIdx.x;
+      if (nu < dim && k < R) tile[threadIdx.x][i] = src[(long long)k * dim + nu];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const long long nu = nu0 + i;
+      const int k = k0 + threadIdx.x;
+      if (nu < dim && k < R) dst[nu * R + k] = tile[i][threadIdx.x];
+    }
+  }
+}
+
+int launch_from_vector_major(const void* src, void* dst, long long dim, int R, int c64, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long tiles = ((dim + 31) / 32) * ((R + 31) / 32);
+  const int grid = (int)(tiles < 152LL * 16 ? tiles : 152LL * 16);
+  const dim3 block(32, 8);
+  if (c64) from_vector_major_kernel<float2><<<grid, block, 0, st>>>((const float2*)src, (float2*)dst, dim, R);
+  else from_vector_major_kernel<double2><<<grid, block, 0, st>>>((const double2*)src, (double2*)dst, dim, R);
+  return (int)cudaGetLastError();
+}
+
 int launch_copy_block(const void* src, void* dst, size_t bytes, void* stream) {
   return (int)cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
 }
