@@ -602,7 +602,8 @@ def run_profile(args):
         F.tune_shape(s, R, "c64", *[int(v) for v in args.shape.split(",")])
     out = F.run(s, R=R, M=M, T=W.temperatures(), seed=spec["seed"], dtype="c64", time_kernels=True)
     return {"mode": "profile_run", "workload": args.hv_workload, "d": s.dim, "R": R, "M": M,
-            "hv_ms_per_launch": out["hv_ms"] / max(1, out["hv_launches"]), "launch_shape": out["shape"]}
+            "hv_ms_per_launch": out["hv_ms"] / max(1, out["hv_launches"]),
+            "device_ms_per_step": out["device_ms"] / M, "launch_shape": out["shape"]}
 
 
 def run_hv_only(args):

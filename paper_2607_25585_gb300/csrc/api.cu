@@ -364,7 +364,7 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
 // Launches one mode of the plan: the spin-1/2 kernel for H.v modes when the
 // plan has it, the general row kernel otherwise.
 int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
-  if (pl.half.on && pl.half.vm && (a.mode == kModeStep || a.mode == kModeStartNorm)) {
+  if (pl.half.on && pl.half.vm && (a.mode == kModeStep || a.mode == kModeStartNorm || a.mode == kModeUpdate)) {
     a.rows_per_tile = pl.half.stream_rows;
     a.tiles_per_vg = pl.half.stream_tiles_per_vg;
     a.n_inst = pl.half.nvg;
@@ -442,6 +442,10 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
   const int grid = streaming ? std::min(pl.grid, 2 * std::max(1, device_sm_count())) : pl.grid;
   return launch_rows(a, pl.c64, grid, pl.sh.threads, pl.smem, st);
 }
+
+// The Lanczos step of the plan runs as the vector-major one-pass gather with
+// the step's w' in its epilogue, then the update pass (see enqueue_run).
+bool vm_fused_step(const Plan& pl) { return pl.half.on && pl.half.vm && pl.half.passes == 1 && !pl.half.hybrid; }
 
 int plan_max_grid(const Plan& pl) {
   return std::max(pl.grid, pl.half.on ? std::max(pl.half.grid, pl.half.stream_grid) : 0);
@@ -627,7 +631,10 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   const bool split = pl.half.on || pl.wideV;
   // single-pass gathers also sum Re<q_j|H q_j>, so alpha_j is known before the
   // epilogue, which then finishes the step in one pass (no separate update)
-  const bool fused = pl.half.on && (pl.half.passes == 1 || pl.half.vm);
+  const bool fused = (pl.half.on && (pl.half.passes == 1 || pl.half.vm)) || (!pl.half.on && pl.wideV);
+  // the vector-major one-pass gather goes further: it writes w' over q_{j-1}
+  // and sums alpha_j and p_j itself; the update pass finishes the step
+  const bool fused_step = vm_fused_step(pl);
   LaunchArgs a = pl.base;
   a.tile_start = reinterpret_cast<const int*>(ctx.tiles.p);
   a.partials = reinterpret_cast<double*>(ctx.partials.p);
@@ -674,6 +681,19 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       if (pl.half.vm) CK(cudaMemcpyAsync(dst, q, vb, cudaMemcpyDeviceToDevice, st));
       else CKI(launch_to_vector_major(q, dst, (long long)s0->hs.dim, R, c64, st));
       ctx.launches++;
+    }
+    if (fused_step) {
+      LaunchArgs g = a;  // x = q_j, y = q_{j-1} (w' in place), u
+      g.mode = kModeApply;
+      g.fused_step = 1;
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      CKI(launch_plan(pl, g, st));
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      a.mode = kModeUpdate;
+      CKI(launch_plan(pl, a, st));
+      ctx.launches += 2;
+      ctx.hv_launches++;
+      continue;
     }
     if (split) {
       LaunchArgs g = a;
@@ -878,7 +898,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     ps = make_plan(sys, R, c64, pl, nullptr, true);
   }
   if (ps != FTLM_OK) return ps;
-  if (pl.half.on) {
+  if (pl.half.on && !vm_fused_step(pl)) {  // (the fused vector-major step keeps no H q block)
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
   } else if (pl.wideV) {

@@ -187,6 +187,44 @@ __device__ __forceinline__ void step_stream(const InstDesc& d, const LaunchArgs&
   }
 }
 
+// kModeUpdate over the groups e, e + step, ... < e_end with U groups' loads in
+// flight per thread before their stores: w -= coef q_j in place, partial |w|^2
+// (summed in the same group order as one group at a time).
+template <typename real, int V, int U>
+__device__ __forceinline__ void update_stream(const InstDesc& d, long long e, long long e_end, long long step,
+                                              const real* coef, real* pacc) {
+  for (; e + (U - 1) * step < e_end; e += U * step) {
+    real wr[U][V], wi[U][V], xr[U][V], xi[U][V];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      VecIO<real, V>::ld(d.y, e + k * step, wr[k], wi[k]);
+      VecIO<real, V>::ldg(d.x, e + k * step, xr[k], xi[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        wr[k][v] = fma(-coef[v], xr[k][v], wr[k][v]);
+        wi[k][v] = fma(-coef[v], xi[k][v], wi[k][v]);
+        pacc[v * kNumPartials] += wr[k][v] * wr[k][v] + wi[k][v] * wi[k][v];
+      }
+      VecIO<real, V>::st(d.y, e + k * step, wr[k], wi[k]);
+    }
+  }
+  for (; e < e_end; e += step) {
+    real wr[V], wi[V], xr[V], xi[V];
+    VecIO<real, V>::ld(d.y, e, wr, wi);
+    VecIO<real, V>::ldg(d.x, e, xr, xi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      wr[v] = fma(-coef[v], xr[v], wr[v]);
+      wi[v] = fma(-coef[v], xi[v], wi[v]);
+      pacc[v * kNumPartials] += wr[v] * wr[v] + wi[v] * wi[v];
+    }
+    VecIO<real, V>::st(d.y, e, wr, wi);
+  }
+}
+
 template <typename real, int V, int MODE>
 __device__ __forceinline__ void elementwise_item(const InstDesc& d, const LaunchArgs& a, long long idx,
                                                  const real* sig, const real* bsp, const real* coef, real* pacc) {
@@ -354,6 +392,11 @@ __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
       sc.alpha[(size_t)j * sc.ss + r] = total_partial(a, inst, r, 0);
       sc.p[((size_t)j * sc.ss + r) * 2] = total_partial(a, inst, r, 1);
       sc.p[((size_t)j * sc.ss + r) * 2 + 1] = total_partial(a, inst, r, 2);
+    } else if (a.mode == kModeApply && a.fused_step) {  // alpha_j = Re<v_j|w'>, p_j = <v_j|u>
+      const double sg = sc.sigma[(size_t)j * sc.ss + r];
+      sc.alpha[(size_t)j * sc.ss + r] = sg * total_partial(a, inst, r, 0);
+      sc.p[((size_t)j * sc.ss + r) * 2] = sg * total_partial(a, inst, r, 1);
+      sc.p[((size_t)j * sc.ss + r) * 2 + 1] = sg * total_partial(a, inst, r, 2);
     } else if (a.mode == kModeApply) {  // gather_alpha
       const double sg = sc.sigma[(size_t)j * sc.ss + r];
       sc.alpha[(size_t)j * sc.ss + r] = sg * sg * total_partial(a, inst, r, 0);

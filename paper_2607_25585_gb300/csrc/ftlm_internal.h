@@ -163,6 +163,11 @@ struct LaunchArgs {
   // vector-major gather of a regular block (inline_one): vector k's x and y
   // are one.x and one.y advanced by k * vm_stride bytes
   long long vm_stride = 0;
+  // vector-major one-pass gather of a Lanczos step (x = q_j, y = q_{j-1}, u):
+  // writes w' = sigma_j H q_j - beta_j sigma_{j-1} q_{j-1} over q_{j-1} and sums
+  // Re<q_j|w'> and <q_j|u>; its last CTA sets alpha_j and p_j.  The rest of
+  // the step, w = w' - alpha_j sigma_j q_j with |w|^2, is kModeUpdate.
+  int fused_step = 0;
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.

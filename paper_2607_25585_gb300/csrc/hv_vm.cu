@@ -146,12 +146,16 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
   constexpr int CB = kLaneBits;  // lane bits [0, CB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDesc d;
-  __shared__ double red[32];
+  __shared__ double wacc[16][3];  // per warp: its units' partial sums for the current vector (FP64)
+  __shared__ double s_sg, s_bsp;  // fused step: sigma_j and beta_j sigma_{j-1} of the current vector
+  __shared__ const void* s_u;     // fused step: the current vector's observable block
   __shared__ int is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const bool kPartials = a.gather_alpha != 0;  // Re<x|Hx> per vector, then alpha_j
+  const bool kPartials = a.gather_alpha != 0 || a.fused_step != 0;  // Re<x|Hx> (or <x|w'>, <x|u>) per vector
+  const bool fused = !MP && a.fused_step != 0;  // the step's w' in the epilogue (one-pass form only)
   const InstDesc* insts = a.inline_one ? &a.one : a.inst;
   if (threadIdx.x == 0) d = insts[0];
+  for (int k = threadIdx.x; k < 16 * 3; k += blockDim.x) wacc[k / 3][k % 3] = 0.0;
   __syncthreads();
   const int n = d.n;
   const int P = MP ? a.npass : 1;
@@ -249,20 +253,40 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
   if (kPartials)  // this CTA's slot of every vector: [vector][CTA][kNumPartials]
     for (int k = threadIdx.x; k < a.n_inst * kNumPartials; k += bd)
       a.partials[((size_t)(k / kNumPartials) * gridDim.x + blockIdx.x) * kNumPartials + k % kNumPartials] = 0.0;
-  // the CTA's sum of its threads' Re<x|Hx> for vector `inst`, in a fixed order
-  auto flush = [&](int inst, double v) {
+  // Partial sums, in a fixed order: each unit's sums are added across the warp
+  // (FP32 shuffles) and into the warp's FP64 slot; flush adds the slots of the
+  // CTA's warps for vector `inst`.  Re<x|Hx> (gather_alpha), or Re<x|w'>,
+  // Re<x|u>, Im<x|u> (fused step).
+  const int np = fused ? 3 : 1;
+  auto add_unit = [&](real p0, real p1, real p2) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+      if (fused) {
+        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+      }
+    }
+    if (lane == 0) {
+      wacc[warp][0] += (double)p0;
+      if (fused) {
+        wacc[warp][1] += (double)p1;
+        wacc[warp][2] += (double)p2;
+      }
+    }
+  };
+  auto flush = [&](int inst) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < np) {  // the sum over the warps, then the slots start again from zero
       double tot = 0.0;
-      for (int w = 0; w < nwarps; ++w) tot += red[w];
-      a.partials[((size_t)inst * gridDim.x + blockIdx.x) * kNumPartials] = tot;
+      for (int w = 0; w < nwarps; ++w) {
+        tot += wacc[w][threadIdx.x];
+        wacc[w][threadIdx.x] = 0.0;
+      }
+      a.partials[((size_t)inst * gridDim.x + blockIdx.x) * kNumPartials + threadIdx.x] = tot;
     }
     __syncthreads();
   };
-  double adot = 0.0;
   int cur = -1;
   const void* x = nullptr;
   void* y0 = nullptr;
@@ -272,8 +296,18 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
     const int pass = MP ? (tile / a.tiles_per_vg) % P : 0;
     const int ptile = tile % a.tiles_per_vg;
     if (inst != cur) {  // per-vector pointers (the tables are shared)
-      if (kPartials && cur >= 0) flush(cur, adot);
-      adot = 0.0;
+      if (kPartials && cur >= 0) flush(cur);
+      if (fused) {
+        __syncthreads();  // every warp is done with the previous vector's scalars
+        if (threadIdx.x == 0) {
+          const DevScalars& sc = insts[inst].sc;
+          const int j = a.step;
+          s_sg = sc.sigma[(size_t)j * sc.ss];
+          s_bsp = a.first ? 0.0 : sc.beta[(size_t)(j - 1) * sc.ss] * sc.sigma[(size_t)(j - 1) * sc.ss];
+          s_u = insts[inst].u;
+        }
+        __syncthreads();
+      }
       if (a.vm_stride) {  // a regular vector-major block: vector inst at a fixed stride
         x = static_cast<const char*>(a.one.x) + (long long)inst * a.vm_stride;
         y0 = static_cast<char*>(a.one.y) + (long long)inst * a.vm_stride;
@@ -348,6 +382,15 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       }
       __syncwarp();
       const long long row0 = (long long)(base | (unsigned long long)lane);
+      if (fused) {  // the epilogue's own rows of q_{j-1} and u to L2 while the unit is gathered
+        const v2* uu = reinterpret_cast<const v2*>(s_u);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const long long e = row0 + ((long long)r << s0);
+          if (!a.first) asm volatile("prefetch.global.L2 [%0];" ::"l"(y + e));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(uu + e));
+        }
+      }
       if (MP && ui + nwarps < units_per_tile && (long long)u + nwarps < nunits) {
         // the warp's next unit: its rows of x (and of y for the top launch) to L2 now,
         // so that the unit's first loads do not wait on HBM
@@ -497,21 +540,48 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r].add(prev[r]);
       }
-      real pd = 0;
+      if (fused) {  // w' = sigma_j H q_j - beta_j sigma_{j-1} q_{j-1} over q_{j-1}; <q_j|w'>, <q_j|u>
+        const v2* uu = reinterpret_cast<const v2*>(s_u);
+        const real sg = (real)s_sg, bsp = (real)s_bsp;
+        real pw = 0, pur = 0, pui = 0;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const v2 hv = acc[r].value();
-        __stcs(MP ? y + ((unsigned)row0 + ((unsigned)r << s0)) : y + row0 + ((long long)r << s0), hv);
-        if (kPartials) {  // the own rows are re-read (L1) rather than kept in registers
-          const v2 xv = ldx_cube<real, MP>(x, row0, r, s0);
-          pd += xv.x * hv.x + xv.y * hv.y;
+        for (int r = 0; r < NR; ++r) {
+          const long long e = row0 + ((long long)r << s0);
+          const v2 hv = acc[r].value();
+          v2 w;
+          if (a.first) {
+            w.x = sg * hv.x;
+            w.y = sg * hv.y;
+          } else {
+            const v2 qp = __ldcs(y + e);
+            w.x = sg * hv.x - bsp * qp.x;
+            w.y = sg * hv.y - bsp * qp.y;
+          }
+          __stcs(y + e, w);
+          const v2 xv = ldx_cube<real, MP>(x, row0, r, s0);  // own rows of q_j, re-read (L1)
+          const v2 uv = __ldcs(uu + e);
+          pw += xv.x * w.x + xv.y * w.y;
+          pur += xv.x * uv.x + xv.y * uv.y;
+          pui += xv.x * uv.y - xv.y * uv.x;
         }
+        add_unit(pw, pur, pui);
+      } else {
+        real pd = 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const v2 hv = acc[r].value();
+          __stcs(MP ? y + ((unsigned)row0 + ((unsigned)r << s0)) : y + row0 + ((long long)r << s0), hv);
+          if (kPartials) {  // the own rows are re-read (L1) rather than kept in registers
+            const v2 xv = ldx_cube<real, MP>(x, row0, r, s0);
+            pd += xv.x * hv.x + xv.y * hv.y;
+          }
+        }
+        if (kPartials) add_unit(pd, (real)0, (real)0);
       }
-      adot += (double)pd;
     }
   }
   if (!kPartials) return;
-  if (cur >= 0) flush(cur, adot);
+  if (cur >= 0) flush(cur);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
@@ -573,6 +643,8 @@ __global__ void __launch_bounds__(256) vm_stream_kernel(const __grid_constant__ 
         sg = (real)d.sc.sigma[(size_t)j * d.sc.ss];
         if (!a.first) bs = (real)(d.sc.beta[(size_t)(j - 1) * d.sc.ss] * d.sc.sigma[(size_t)(j - 1) * d.sc.ss]);
         cf = (real)(d.sc.alpha[(size_t)j * d.sc.ss] * d.sc.sigma[(size_t)j * d.sc.ss]);
+      } else if (MODE == kModeUpdate) {  // the tail of the fused step: w = w' - alpha_j sigma_j q_j
+        cf = (real)(d.sc.alpha[(size_t)j * d.sc.ss] * d.sc.sigma[(size_t)j * d.sc.ss]);
       }
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -591,6 +663,8 @@ __global__ void __launch_bounds__(256) vm_stream_kernel(const __grid_constant__ 
     long long e = e0 + (long long)threadIdx.x * V;
     if (MODE == kModeStep) {
       step_stream<real, V, 4>(d, a, e, e_end, step, sig, bsp, coef, pacc);
+    } else if (MODE == kModeUpdate) {
+      update_stream<real, V, 4>(d, e, e_end, step, coef, pacc);
     } else {
       for (; e + step < e_end; e += 2 * step) {
         elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);
@@ -623,6 +697,9 @@ int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream) {
   if (a.mode == kModeStep) {
     if (c64) vm_stream_kernel<float, kModeStep><<<grid, 256, 0, st>>>(a);
     else vm_stream_kernel<double, kModeStep><<<grid, 256, 0, st>>>(a);
+  } else if (a.mode == kModeUpdate) {
+    if (c64) vm_stream_kernel<float, kModeUpdate><<<grid, 256, 0, st>>>(a);
+    else vm_stream_kernel<double, kModeUpdate><<<grid, 256, 0, st>>>(a);
   } else if (a.mode == kModeStartNorm) {
     if (c64) vm_stream_kernel<float, kModeStartNorm><<<grid, 256, 0, st>>>(a);
     else vm_stream_kernel<double, kModeStartNorm><<<grid, 256, 0, st>>>(a);

@@ -8,7 +8,7 @@
 // q_j at the row itself and at its single-site neighbours mu -+ stride_k.
 //
 // One kernel does both halves: a CTA owns one vector r, a 64 x 64 block of
-// (i, j) and a range of rows.  Per tile of 32 rows (16 in complex128) it stages q_i (the i block)
+// (i, j) and a range of rows.  Per tile of 64 rows (32 in complex128) it stages q_i (the i block)
 // and (u.S) q_j (the j block, formed from the neighbours on the fly) in
 // shared memory, and every thread accumulates 4 x 4 entries of G (rows
 // ti + 16a, columns tj + 16b of the block) in registers.  (u.S) q_j is never
@@ -32,19 +32,28 @@ namespace {
 constexpr int kSymBlock = 64;  // i and j block
 constexpr int kSymThreads = 256;
 
-// rows per shared-memory tile: 32 complex64 or 16 complex128 (under 48 KB)
+// rows per shared-memory tile: 64 complex64 or 32 complex128
 template <typename real>
 struct SymRows {
-  static constexpr int value = sizeof(real) == 4 ? 32 : 16;
+  static constexpr int value = sizeof(real) == 4 ? 64 : 32;
 };
 
+// Dynamic shared memory: the A and B tiles, the row digits [site][row], the
+// S^z sums of the rows, and the site tables (m, <a|s+|a-1>, <a|s-|a+1>) with
+// the radices and strides.
 template <typename real>
-struct SymSmem {
+struct SymLayout {
   static constexpr int kRows = SymRows<real>::value;
-  typename Cx<real>::v2 A[kSymBlock][kRows + 1];  // q_i[mu], i in the i block
-  typename Cx<real>::v2 B[kSymBlock][kRows + 1];  // ((u.S) q_j)[mu], j in the j block
-  real msum[kRows];                               // sum_k m_k(mu)
-  unsigned char dig[kRows][kMaxSites];            // digits a_k(mu)
+  static constexpr int kPitch = kRows + 1;
+  static size_t tile_bytes() { return sizeof(typename Cx<real>::v2) * kSymBlock * kPitch; }
+  static size_t bytes(int n, int qm) {
+    size_t b = 2 * tile_bytes();
+    b += (size_t)kRows * sizeof(real);                          // msum
+    b += (((size_t)n * kRows + 15) / 16) * 16;                  // digits
+    b += (((size_t)3 * n * qm * sizeof(real) + 15) / 16) * 16;  // m, up1, dn1
+    b += (size_t)n * 8 + (size_t)n * 4;                         // strides, radices
+    return b;
+  }
 };
 
 // grid: x = row range, y = (i block, j block), z = vector r.  Gp partials
@@ -54,8 +63,21 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
                                                              int M, long long rows_per_range, int nbj,
                                                              double* __restrict__ Gp) {
   using v2 = typename Cx<real>::v2;
-  constexpr int kSymRows = SymRows<real>::value;
-  __shared__ SymSmem<real> S;
+  using Lay = SymLayout<real>;
+  constexpr int kRows = Lay::kRows, kPitch = Lay::kPitch;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = d.n, qm = d.lay.qmax;
+  v2* A = reinterpret_cast<v2*>(smem);                       // [kSymBlock][kPitch]
+  v2* B = A + kSymBlock * kPitch;                            // [kSymBlock][kPitch]
+  real* msum = reinterpret_cast<real*>(B + kSymBlock * kPitch);
+  unsigned char* dig = reinterpret_cast<unsigned char*>(msum + kRows);  // [n][kRows]
+  real* tm = reinterpret_cast<real*>(dig + (((size_t)n * kRows + 15) / 16) * 16);  // [n][qm]
+  real* tup = tm + n * qm;
+  real* tdn = tup + n * qm;
+  long long* sst = reinterpret_cast<long long*>(
+      reinterpret_cast<unsigned char*>(tm) + (((size_t)3 * n * qm * sizeof(real) + 15) / 16) * 16);
+  int* sq = reinterpret_cast<int*>(sst + n);
+
   const int r = blockIdx.z;
   const int ib = blockIdx.y / nbj, jb = blockIdx.y % nbj;
   const int i0 = ib * kSymBlock, j0 = jb * kSymBlock;
@@ -63,51 +85,75 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
   const long long dim = d.dim;
   const long long mu_lo = (long long)blockIdx.x * rows_per_range;
   const long long mu_hi = min(dim, mu_lo + rows_per_range);
-  const real* t = reinterpret_cast<const real*>(d.tab);
-  const TabLayout& L = d.lay;
-  const int qm = L.qmax, n = d.n;
   const real uz = (real)d.obs[0], aur = (real)d.obs[1], aui = (real)d.obs[2];
   const size_t vstride = (size_t)R * (size_t)dim;  // elements between steps k and k + 1
   const v2* base = reinterpret_cast<const v2*>(Vs) + (size_t)r * (size_t)dim;
+  {
+    const real* t = reinterpret_cast<const real*>(d.tab);
+    for (int e = threadIdx.x; e < n * qm; e += blockDim.x) {
+      tm[e] = t[d.lay.off_m + e];
+      tup[e] = t[d.lay.off_up1 + e];
+      tdn[e] = t[d.lay.off_dn1 + e];
+    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      sst[k] = d.stride[k];
+      sq[k] = d.q[k];
+    }
+  }
   // this thread's entries of the 64 x 64 block: rows ti + 16a, columns tj + 16b
-  // (a half-warp reads 16 consecutive rows of B: no bank conflicts)
+  // (a half-warp reads 16 consecutive rows of B: no bank conflicts); a thread
+  // skips the rows and columns beyond M (warp-uniform for the rows)
   const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
+  const int na = (ni - ti + 15) / 16, nbb = (nj - tj + 15) / 16;
   real gr[4][4], gi[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) gr[a][b] = gi[a][b] = 0;
+  const bool idx32 = dim <= 0xffffffffll;
 
-  for (long long m0 = mu_lo; m0 < mu_hi; m0 += kSymRows) {
-    const int nt = (int)min((long long)kSymRows, mu_hi - m0);
+  for (long long m0 = mu_lo; m0 < mu_hi; m0 += kRows) {
+    const int nt = (int)min((long long)kRows, mu_hi - m0);
     __syncthreads();
     // digits and the S^z sum of the tile's rows
     for (int tt = threadIdx.x; tt < nt; tt += blockDim.x) {
-      unsigned long long rem = (unsigned long long)(m0 + tt);
       real ms = 0;
-      for (int k = 0; k < n; ++k) {
-        const unsigned qk = (unsigned)__ldg(d.q + k);
-        const unsigned long long nq = rem / qk;
-        const int a = (int)(rem - nq * qk);
-        rem = nq;
-        S.dig[tt][k] = (unsigned char)a;
-        ms += t[L.off_m + k * qm + a];
+      if (idx32) {
+        unsigned rem = (unsigned)(m0 + tt);
+        for (int k = 0; k < n; ++k) {
+          const unsigned qk = (unsigned)sq[k];
+          const unsigned nq = rem / qk;
+          const int a = (int)(rem - nq * qk);
+          rem = nq;
+          dig[k * kRows + tt] = (unsigned char)a;
+          ms += tm[k * qm + a];
+        }
+      } else {
+        unsigned long long rem = (unsigned long long)(m0 + tt);
+        for (int k = 0; k < n; ++k) {
+          const unsigned long long qk = (unsigned long long)sq[k];
+          const unsigned long long nq = rem / qk;
+          const int a = (int)(rem - nq * qk);
+          rem = nq;
+          dig[k * kRows + tt] = (unsigned char)a;
+          ms += tm[k * qm + a];
+        }
       }
-      S.msum[tt] = ms;
+      msum[tt] = ms;
     }
     // q_i of the i block
-    for (int e = threadIdx.x; e < kSymBlock * kSymRows; e += blockDim.x) {
-      const int ii = e / kSymRows, tt = e % kSymRows;
+    for (int e = threadIdx.x; e < kSymBlock * kRows; e += blockDim.x) {
+      const int ii = e / kRows, tt = e % kRows;
       v2 v;
       v.x = 0;
       v.y = 0;
       if (ii < ni && tt < nt) v = __ldg(base + (size_t)(i0 + ii) * vstride + (size_t)(m0 + tt));
-      S.A[ii][tt] = v;
+      A[ii * kPitch + tt] = v;
     }
     __syncthreads();
     // (u.S) q_j of the j block from the single-site neighbours
-    for (int e = threadIdx.x; e < kSymBlock * kSymRows; e += blockDim.x) {
-      const int jj = e / kSymRows, tt = e % kSymRows;
+    for (int e = threadIdx.x; e < kSymBlock * kRows; e += blockDim.x) {
+      const int jj = e / kRows, tt = e % kRows;
       v2 o;
       o.x = 0;
       o.y = 0;
@@ -116,44 +162,46 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
         const long long mu = m0 + tt;
         real ar = 0, ai = 0;
         for (int k = 0; k < n; ++k) {
-          const int a = S.dig[tt][k];
-          const int qk = __ldg(d.q + k);
-          const long long st = __ldg(d.stride + k);
+          const int a = dig[k * kRows + tt];
+          const long long st = sst[k];
           if (a >= 1) {  // a S^+ : from mu - stride
-            const real c = t[L.off_up1 + k * qm + a];
+            const real c = tup[k * qm + a];
             const v2 xv = __ldg(x + mu - st);
             ar += c * (aur * xv.x - aui * xv.y);
             ai += c * (aur * xv.y + aui * xv.x);
           }
-          if (a + 1 < qk) {  // conj(a) S^- : from mu + stride
-            const real c = t[L.off_dn1 + k * qm + a];
+          if (a + 1 < sq[k]) {  // conj(a) S^- : from mu + stride
+            const real c = tdn[k * qm + a];
             const v2 xv = __ldg(x + mu + st);
             ar += c * (aur * xv.x + aui * xv.y);
             ai += c * (aur * xv.y - aui * xv.x);
           }
         }
         const v2 xv = __ldg(x + mu);
-        const real dz = uz * S.msum[tt];
+        const real dz = uz * msum[tt];
         o.x = ar + dz * xv.x;
         o.y = ai + dz * xv.y;
       }
-      S.B[jj][tt] = o;
+      B[jj * kPitch + tt] = o;
     }
     __syncthreads();
     // G[i][j] += conj(A[i][mu]) B[j][mu]
     for (int tt = 0; tt < nt; ++tt) {
       v2 av[4], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = S.A[ti + 16 * a][tt];
+      for (int a = 0; a < 4; ++a) av[a] = A[(ti + 16 * a) * kPitch + tt];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = S.B[tj + 16 * b][tt];
+      for (int b = 0; b < 4; ++b) bv[b] = B[(tj + 16 * b) * kPitch + tt];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a) {
+        if (a >= na) break;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
+          if (b >= nbb) break;
           gr[a][b] = fma(av[a].x, bv[b].x, fma(av[a].y, bv[b].y, gr[a][b]));
           gi[a][b] = fma(av[a].x, bv[b].y, fma(-av[a].y, bv[b].x, gi[a][b]));
         }
+      }
     }
   }
   // this CTA's partial block
@@ -163,7 +211,7 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * b;
-      if (ti + 16 * a < ni && tj + 16 * b < nj) {
+      if (a < na && b < nbb) {
         out[2 * ((size_t)i * M + j)] = (double)gr[a][b];
         out[2 * ((size_t)i * M + j) + 1] = (double)gi[a][b];
       }
@@ -208,9 +256,20 @@ int launch_sym_omat(const InstDesc* h, const void* Vs, int R, int M, int nranges
   if ((long long)nb * nb > 65535) return (int)cudaErrorInvalidValue;
   const long long rows = (h->dim + nranges - 1) / nranges;
   const dim3 grid((unsigned)nranges, (unsigned)(nb * nb), (unsigned)R);
-  if (c64) sym_omat_kernel<float><<<grid, kSymThreads, 0, st>>>(*h, (const float*)Vs, R, M, rows, nb, Gp);
-  else sym_omat_kernel<double><<<grid, kSymThreads, 0, st>>>(*h, (const double*)Vs, R, M, rows, nb, Gp);
-  cudaError_t e = cudaGetLastError();
+  const int qm = h->lay.qmax;
+  cudaError_t e;
+  if (c64) {
+    const size_t smem = SymLayout<float>::bytes(h->n, qm);
+    e = cudaFuncSetAttribute(sym_omat_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    sym_omat_kernel<float><<<grid, kSymThreads, smem, st>>>(*h, (const float*)Vs, R, M, rows, nb, Gp);
+  } else {
+    const size_t smem = SymLayout<double>::bytes(h->n, qm);
+    e = cudaFuncSetAttribute(sym_omat_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    sym_omat_kernel<double><<<grid, kSymThreads, smem, st>>>(*h, (const double*)Vs, R, M, rows, nb, Gp);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
   const long long total = (long long)R * M * M;
   sym_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Gp, R, M, nranges, G);
