@@ -296,9 +296,8 @@ def precision_legs(F, T, stream, args, s_head, spec_head, res_head):
     per temperature: the 4x5 lattice at its full R = 64, M = 200 (the c64 run
     is the headline's last timed run; the c128 run of the whole block is also
     the batched-FP64 throughput) and the 2x13 ladder at M = 300 (both timed as
-    full runs) with --ladder-precision-R vectors: 4, the workload's R, takes
-    about three minutes in FP64 (bound by the FP64 pipes), so the default
-    compares one vector."""
+    full runs) with its R = 4 vectors (--ladder-precision-R; the FP64 run
+    takes about three minutes, bound by the FP64 pipes)."""
     out = {}
     R, M = spec_head["R"], args.M or spec_head["M"]
     d = s_head.dim
@@ -606,6 +605,35 @@ def run_profile(args):
             "device_ms_per_step": out["device_ms"] / M, "launch_shape": out["shape"]}
 
 
+def run_profile_batch(args):
+    """One run of the uneven batch (24 s = 1 chains x field directions, R = 16,
+    M = 120, complex64, one graph) with the library's default launch shape
+    (which the autotuner also picks for it): device time of the whole graph
+    from CUDA events, for comparison with the summed kernel durations of an
+    ncu launch list of the same command (the difference is the launch gaps)."""
+    import torch
+
+    import paper_2607_25585_gb300 as F
+
+    F.build()
+    spec = W.WORKLOADS["chains_s1_x24"]
+    systems = [F.System.from_dict(w) for w in spec["system"]()]
+    R, M = spec["R"], spec["M"]
+    T = W.temperatures()
+    stream = torch.cuda.Stream()
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream)
+    F.run_batch(systems, **kw)  # captures the graph
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = F.run_batch(systems, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"mode": "profile_batch", "instances": len(systems), "R": R, "M": M,
+            "graph_ms": e0.elapsed_time(e1), "kernel_launches": res[0]["kernel_launches"],
+            "launch_shape": res[0]["shape"]}
+
+
 def run_hv_only(args):
     """ftlm_apply_h alone: args.hv_only launches of H.v on the workload's
     row-major [d][R] complex64 block (the row-major kernels, as a caller of
@@ -651,8 +679,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 legs")
     ap.add_argument("--no-ladder-precision", action="store_true", help="skip the 2x13 ladder in the FP32-vs-FP64 legs")
-    ap.add_argument("--ladder-precision-R", type=int, default=1,
-                    help="vectors of the 2x13 ladder's FP32-vs-FP64 comparison (the workload's R is 4)")
+    ap.add_argument("--ladder-precision-R", type=int, default=4,
+                    help="vectors of the 2x13 ladder's FP32-vs-FP64 comparison (the workload's R, 4, by default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and ladder measurements")
     ap.add_argument("--ladder-steps", type=int, default=20)
@@ -662,12 +690,16 @@ def main():
                     help="workload of --hv-only (a batch uses its largest instance)")
     ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] for the main run")
     ap.add_argument("--profile-run", default="", help="R,M: one short run of --hv-workload (for profilers)")
+    ap.add_argument("--profile-batch", action="store_true", help="one run of the 24-chain batch (for profilers)")
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate launch shapes first (default: the library's default plan, which "
                          "keeps the command's kernels the same under a profiler)")
     args = ap.parse_args()
     if args.profile_run:
         print(json.dumps(run_profile(args)))
+        return
+    if args.profile_batch:
+        print(json.dumps(run_profile_batch(args)))
         return
     if args.hv_only:
         print(json.dumps(run_hv_only(args)), flush=True)

@@ -237,9 +237,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
         }
         if (MODE == kModeApply) {
           VecIO<real, V>::st(d.y, idx, ar, ai);
-          if (kPartials) {  // Re<x|Hx> of the row (its own x came with the gather)
+          if (kPartials) {  // Re<x|Hx> of the row: its own x re-read (L1) rather than kept live
+            real ox[V], oy[V];
+            VecIO<real, V>::ldg(d.x, idx, ox, oy);
 #pragma unroll
-            for (int v = 0; v < V; ++v) pacc_alpha[v] += xr[v] * ar[v] + xi[v] * ai[v];
+            for (int v = 0; v < V; ++v) pacc_alpha[v] += ox[v] * ar[v] + oy[v] * ai[v];
           }
         } else {
           real wr[V], wi[V];
