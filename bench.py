@@ -218,6 +218,7 @@ def run_ours(args):
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": traffic, "algorithmic_flops_per_sv": flops_sv,
                          "hv_ms_per_launch": hv_per_launch_ms, "launch_shape": results["shape"],
+                         "launch_gap_ms_per_step": results["gap_ms"] / max(1, M - 1),
                          "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"},
             "hbm": {"bytes_per_sv": 32, "peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                     "frac": value / ws * 32 / (hbm * 1e9)},
@@ -366,6 +367,8 @@ def extra_workloads(F, T, stream, args):
     sv = sum(s.dim for s in systems) * R * M
     out["chains_s1_x24"] = {"value": sv / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R,
                             "instances": len(systems), "hv_ms_per_launch": res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
+                            "launch_gap_ms_per_step": res[0]["gap_ms"] / max(1, M - 1),
+                            "launch_gap_share": res[0]["gap_ms"] / max(1e-9, res[0]["device_ms"]),
                             "launch_shape": res[0]["shape"], "autotuned": True,
                             "note": "one graph for all 24 instances; shape chosen by the autotuner"}
     for s in systems:

@@ -263,6 +263,9 @@ typedef struct {
   double* M_B_sym_imag;   /* [nT] imaginary part of that numerator, a diagnostic */
   double* O_lanczos;      /* [R][M][M][2] complex O_ij = <v_i|u.S|v_j> (row-major; zero beyond M_eff) */
   double sym_ms;          /* device time of forming O (after the Lanczos run) */
+  double gap_ms;          /* time_kernels = 1: summed device time between the end of one Lanczos
+                             step's last launch and the start of the next step's first launch
+                             (the graph's launch gaps; M - 1 of them) */
 } ftlm_result;
 
 /*

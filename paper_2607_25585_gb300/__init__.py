@@ -62,6 +62,7 @@ class Result(ctypes.Structure):
         ("grid", ctypes.c_int), ("threads", ctypes.c_int), ("vector_major", ctypes.c_int),
         ("M_B_sym", ctypes.POINTER(ctypes.c_double)), ("M_B_sym_imag", ctypes.POINTER(ctypes.c_double)),
         ("O_lanczos", ctypes.POINTER(ctypes.c_double)), ("sym_ms", ctypes.c_double),
+        ("gap_ms", ctypes.c_double),
     ]
 
 
@@ -337,7 +338,7 @@ def _result(R, M, nT, keep, symmetric=False):
 
 
 def _finish(r, out):
-    out.update(E0=r.E0, device_ms=r.device_ms, hv_ms=r.hv_ms, hv_launches=r.hv_launches,
+    out.update(E0=r.E0, device_ms=r.device_ms, hv_ms=r.hv_ms, gap_ms=r.gap_ms, hv_launches=r.hv_launches,
                kernel_launches=r.kernel_launches, h2d_bytes=int(r.h2d_bytes), d2h_bytes=int(r.d2h_bytes),
                shape={"cube_bits": r.cube_bits, "passes": r.passes, "group_vectors": r.group_vectors,
                       "tile_rows": r.tile_rows,

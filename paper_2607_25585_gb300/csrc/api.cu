@@ -672,6 +672,14 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
     a.inst = (j % 2 == 0) ? d_even : d_odd;
     a.step = j;
     a.first = j == 0;
+    // time_kernels: events at the step's start and end and around its H.v launch
+    // ([1 + 4j] .. [4 + 4j]); a step's start event follows the previous step's
+    // end event with no work between them, so their difference is the gap
+    // between two launches of the graph
+    if (tk) {
+      evi = 1 + 4 * j;
+      CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+    }
     if (p->symmetric || p->reorth) {  // keep q_j (vector-major): the matrix of u.S in the Lanczos basis, or
                                        // the vectors the next ones are re-orthogonalised against
       ftlm_system* s0 = sys[0];
@@ -693,6 +701,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       CKI(launch_plan(pl, a, st));
       ctx.launches += 2;
       ctx.hv_launches++;
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[4 + 4 * j], st, cudaEventRecordExternal));
       continue;
     }
     if (split) {
@@ -711,6 +720,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
         a.hq_parts = 1;
         ctx.launches += 2;
         ctx.hv_launches++;
+        if (tk) CK(cudaEventRecordWithFlags(ctx.ev[4 + 4 * j], st, cudaEventRecordExternal));
         continue;
       }
       a.mode = kModeEpilogue;
@@ -739,8 +749,9 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       a.update_no_alpha = 0;
       ctx.launches += 5;
     }
+    if (tk) CK(cudaEventRecordWithFlags(ctx.ev[4 + 4 * j], st, cudaEventRecordExternal));
   }
-  if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+  if (tk) CK(cudaEventRecordWithFlags(ctx.ev[4 * M + 1], st, cudaEventRecordExternal));
   const size_t per = staged_bytes(R, M);
   for (int k = 0; k < n; ++k) {  // alpha, beta, p, M_eff -> pinned host staging
     DevScalars sc = scalars_at(sys[k]->scal.p, R, M);
@@ -803,7 +814,7 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
   c.h2d = sizeof(InstDesc) * h.size() + sizeof(int) * pl.tile_start.size();
   CK(cudaMallocHost(reinterpret_cast<void**>(&c.pinned), staged_bytes(R, M) * n));
   if (p->time_kernels) {
-    c.ev.resize(2 * M + 2);
+    c.ev.resize(4 * M + 2);
     for (auto& e : c.ev) CK(cudaEventCreate(&e));
   }
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -954,15 +965,19 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   CK(cudaStreamWaitEvent(caller, sys[0]->ev_out, 0));  // the caller's later work sees the run complete
   CK(cudaStreamSynchronize(st));
   const auto t1 = std::chrono::steady_clock::now();
-  double hv_ms = 0.0, dev_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  double hv_ms = 0.0, gap_ms = 0.0, dev_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   if (p->time_kernels && !ctx->ev.empty()) {
     for (int j = 0; j < M; ++j) {
       float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ctx->ev[1 + 2 * j], ctx->ev[2 + 2 * j]));
+      CK(cudaEventElapsedTime(&ms, ctx->ev[2 + 4 * j], ctx->ev[3 + 4 * j]));
       hv_ms += ms;
+      if (j + 1 < M) {
+        CK(cudaEventElapsedTime(&ms, ctx->ev[4 + 4 * j], ctx->ev[1 + 4 * (j + 1)]));
+        gap_ms += ms;
+      }
     }
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2 * M + 1]));
+    CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[4 * M + 1]));
     dev_ms = ms;
   }
   const size_t per = staged_bytes(R, M);
@@ -994,6 +1009,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     if (out.M_eff) std::memcpy(out.M_eff, me.data(), sizeof(int) * R);
     out.device_ms = dev_ms;
     out.hv_ms = hv_ms;
+    out.gap_ms = gap_ms;
     out.hv_launches = ctx->hv_launches;
     out.kernel_launches = ctx->launches;
     out.h2d_bytes = k == 0 ? h2d : 0;

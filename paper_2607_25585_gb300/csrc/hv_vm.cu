@@ -253,12 +253,14 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
   if (kPartials)  // this CTA's slot of every vector: [vector][CTA][kNumPartials]
     for (int k = threadIdx.x; k < a.n_inst * kNumPartials; k += bd)
       a.partials[((size_t)(k / kNumPartials) * gridDim.x + blockIdx.x) * kNumPartials + k % kNumPartials] = 0.0;
-  // Partial sums, in a fixed order: each unit's sums are added across the warp
-  // (FP32 shuffles) and into the warp's FP64 slot; flush adds the slots of the
-  // CTA's warps for vector `inst`.  Re<x|Hx> (gather_alpha), or Re<x|w'>,
-  // Re<x|u>, Im<x|u> (fused step).
+  // Partial sums, in a fixed order: each thread's sums over its rows of a unit
+  // are added across the warp in FP64 (the Lanczos scalars need FP64 sums:
+  // alpha_j and p_j feed the Ritz values and weights) and into the warp's FP64
+  // slot; flush adds the slots of the CTA's warps for vector `inst`.
+  // Re<x|Hx> (gather_alpha), or Re<x|w'>, Re<x|u>, Im<x|u> (fused step).
   const int np = fused ? 3 : 1;
-  auto add_unit = [&](real p0, real p1, real p2) {
+  auto add_unit = [&](real p0f, real p1f, real p2f) {
+    double p0 = (double)p0f, p1 = (double)p1f, p2 = (double)p2f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       p0 += __shfl_xor_sync(0xffffffffu, p0, o);
@@ -268,10 +270,10 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       }
     }
     if (lane == 0) {
-      wacc[warp][0] += (double)p0;
+      wacc[warp][0] += p0;
       if (fused) {
-        wacc[warp][1] += (double)p1;
-        wacc[warp][2] += (double)p2;
+        wacc[warp][1] += p1;
+        wacc[warp][2] += p2;
       }
     }
   };

@@ -164,7 +164,12 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
   }
   int cur = -1;
   real sig[V], bsp[V], coef[V];  // per-vector scalars of the current instance
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  // each CTA takes a contiguous range of the tile list, so it meets few
+  // instance boundaries (each one flushes the partial sums)
+  const int tiles_per_cta = (a.ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int tile_lo = (int)blockIdx.x * tiles_per_cta;
+  const int tile_hi = min(a.ntiles, tile_lo + tiles_per_cta);
+  for (int tile = tile_lo; tile < tile_hi; ++tile) {
     const int inst = a.inline_one ? 0 : find_instance(a.tile_start, a.n_inst, tile);
     if (inst != cur) {
       if (kPartialsMode && cur >= 0) flush_partials<V>(a, s, cur, acc);
