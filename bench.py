@@ -265,15 +265,19 @@ def measured_traffic(shape):
 def per_t_errors(a, b, T, floor=1e-3):
     """Relative error of every thermodynamic result of run a against run b at
     each temperature, with a floor of `floor` times the quantity's maximum
-    over T (quantities that pass through zero), and its maximum over
-    T >= 0.1 K."""
+    over T (quantities that pass through zero), its maximum over T >= 0.1 K,
+    the absolute error over T >= 0.1 K on the scale of the quantity's largest
+    value, and run b's values."""
     out = {}
     cold = T >= 0.1
     for k in ("lnZ", "E", "C", "M_B"):
         x, y = np.asarray(a[k]), np.asarray(b[k])
         e = np.abs(x - y) / np.maximum(np.abs(y), floor * np.max(np.abs(y)))
         out[k] = {"max_T_ge_0.1": float(e[cold].max()), "max_all_T": float(e.max()),
-                  "per_T": [float(v) for v in e]}
+                  "per_T": [float(v) for v in e],
+                  # the absolute error on the scale of the quantity (its largest |value| over T)
+                  "abs_over_max_T_ge_0.1": float((np.abs(x - y)[cold]).max() / np.max(np.abs(y))),
+                  "fp64_per_T": [float(v) for v in y]}
     out["max_T_ge_0.1"] = max(out[k]["max_T_ge_0.1"] for k in ("lnZ", "E", "C", "M_B"))
     return out
 

@@ -631,7 +631,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   const bool split = pl.half.on || pl.wideV;
   // single-pass gathers also sum Re<q_j|H q_j>, so alpha_j is known before the
   // epilogue, which then finishes the step in one pass (no separate update)
-  const bool fused = (pl.half.on && (pl.half.passes == 1 || pl.half.vm)) || (!pl.half.on && pl.wideV);
+  const bool fused = pl.half.on && (pl.half.passes == 1 || pl.half.vm);
   // the vector-major one-pass gather goes further: it writes w' over q_{j-1}
   // and sums alpha_j and p_j itself; the update pass finishes the step
   const bool fused_step = vm_fused_step(pl);

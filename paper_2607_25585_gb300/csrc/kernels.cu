@@ -104,26 +104,6 @@ __device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst,
   for (int k = 0; k < np; ++k) acc[k] = 0.0;
 }
 
-// The same for H.v with gather_alpha: one partial (Re<x|Hx>) per vector, in
-// slot 0 of the partials (the other slots stay zero), from the threads' sums
-// in s.red[thread][v], which start again from zero.
-template <int V>
-__device__ void flush_alpha(const LaunchArgs& a, const SmemView& s, int inst) {
-  __syncthreads();
-  const int C = a.C;
-  const int per = blockDim.x / C;
-  if ((int)threadIdx.x < C) {
-    double* out = a.partials + ((size_t)inst * gridDim.x + blockIdx.x) * (size_t)a.R * kNumPartials;
-    for (int v = 0; v < V; ++v) {
-      double sum = 0.0;
-      for (int r = 0; r < per; ++r) sum += s.red[(threadIdx.x + r * C) * V + v];
-      out[(threadIdx.x * V + v) * kNumPartials] = sum;
-    }
-  }
-  __syncthreads();
-  for (int v = 0; v < V; ++v) s.red[threadIdx.x * V + v] = 0.0;
-}
-
 // ---------------------------------------------------------------------------
 // the tile loop shared by every mode
 // ---------------------------------------------------------------------------
@@ -131,26 +111,16 @@ template <typename real, int V, int MODE>
 // complex64: three 256-thread CTAs per SM (at most 85 registers a thread)
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(const __grid_constant__ LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool kPartialsMode = MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate ||
-                                 MODE == kModeStartNorm || MODE == kModeStep;
-  // H.v may also sum Re<x|Hx> per vector (alpha_j of a Lanczos step, gather_alpha):
-  // its partials use slot 0 only, the reduction space holds V doubles a thread
-  const bool kPartials = kPartialsMode || (MODE == kModeApply && a.gather_alpha != 0);
-  // (carve reserves blockDim * kNumPartials * its V argument doubles; H.v's alpha
-  // sums need blockDim * V)
-  const SmemView s =
-      carve<real>(smem_raw, a, kPartialsMode ? V : (MODE == kModeApply ? (V + kNumPartials - 1) / kNumPartials : 0));
+  constexpr bool kPartials = MODE == kModeLanczos || MODE == kModeEpilogue || MODE == kModeUpdate ||
+                             MODE == kModeStartNorm || MODE == kModeStep;
+  const SmemView s = carve<real>(smem_raw, a, kPartials ? V : 0);  // no reduction space without partial sums
   __shared__ InstDesc d;
   __shared__ int is_last;
   const InstDesc* insts = a.inline_one ? &a.one : a.inst;
   constexpr int NP = V * kNumPartials;
-  double acc[kPartialsMode ? NP : 1];
+  double acc[NP];
 #pragma unroll
-  for (int k = 0; k < (kPartialsMode ? NP : 1); ++k) acc[k] = 0.0;
-  // gather_alpha: each thread sums Re<x|Hx> of its vectors over its tiles in
-  // its own FP64 slots of the reduction space (s.red[thread][v])
-  if (MODE == kModeApply && kPartials)
-    for (int v = 0; v < V; ++v) s.red[threadIdx.x * V + v] = 0.0;
+  for (int k = 0; k < NP; ++k) acc[k] = 0.0;
 
   const int C = a.C;
   const int chunk = threadIdx.x % C;   // fixed per thread: blockDim is a multiple of C
@@ -164,16 +134,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
   }
   int cur = -1;
   real sig[V], bsp[V], coef[V];  // per-vector scalars of the current instance
-  // each CTA takes a contiguous range of the tile list, so it meets few
-  // instance boundaries (each one flushes the partial sums)
-  const int tiles_per_cta = (a.ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int tile_lo = (int)blockIdx.x * tiles_per_cta;
-  const int tile_hi = min(a.ntiles, tile_lo + tiles_per_cta);
-  for (int tile = tile_lo; tile < tile_hi; ++tile) {
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int inst = a.inline_one ? 0 : find_instance(a.tile_start, a.n_inst, tile);
     if (inst != cur) {
-      if (kPartialsMode && cur >= 0) flush_partials<V>(a, s, cur, acc);
-      if (MODE == kModeApply && kPartials && cur >= 0) flush_alpha<V>(a, s, cur);
+      if (kPartials && cur >= 0) flush_partials<V>(a, s, cur, acc);
       __syncthreads();
       if (threadIdx.x == 0) d = insts[inst];
       __syncthreads();
@@ -203,12 +167,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
     const int first_tile = a.inline_one ? 0 : __ldg(a.tile_start + inst);
     const long long row0 = (long long)(tile - first_tile) * a.rows_per_tile;
     const bool idx32 = d.dim <= 0xffffffffll;
-    real pacc[kPartialsMode ? NP : 1];
+    real pacc[NP];
 #pragma unroll
-    for (int k = 0; k < (kPartialsMode ? NP : 1); ++k) pacc[k] = 0;
-    real pacc_alpha[MODE == kModeApply ? V : 1];
-#pragma unroll
-    for (int v = 0; v < (MODE == kModeApply ? V : 1); ++v) pacc_alpha[v] = 0;
+    for (int k = 0; k < NP; ++k) pacc[k] = 0;
     constexpr bool kElementwise = MODE == kModeEpilogue || MODE == kModeUpdate || MODE == kModeStartNorm ||
                                   MODE == kModeScale || MODE == kModeStep;
     if (kElementwise) {
@@ -242,12 +203,6 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
         }
         if (MODE == kModeApply) {
           VecIO<real, V>::st(d.y, idx, ar, ai);
-          if (kPartials) {  // Re<x|Hx> of the row: its own x re-read (L1) rather than kept live
-            real ox[V], oy[V];
-            VecIO<real, V>::ldg(d.x, idx, ox, oy);
-#pragma unroll
-            for (int v = 0; v < V; ++v) pacc_alpha[v] += ox[v] * ar[v] + oy[v] * ai[v];
-          }
         } else {
           real wr[V], wi[V];
           if (!a.first) {
@@ -314,18 +269,13 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
       }
     }
     }
-    if (kPartialsMode) {
+    if (kPartials) {
 #pragma unroll
       for (int k = 0; k < NP; ++k) acc[k] += (double)pacc[k];
     }
-    if (MODE == kModeApply && kPartials) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) s.red[threadIdx.x * V + v] += (double)pacc_alpha[v];
-    }
   }
   if (!kPartials) return;
-  if (kPartialsMode && cur >= 0) flush_partials<V>(a, s, cur, acc);
-  if (MODE == kModeApply && cur >= 0) flush_alpha<V>(a, s, cur);
+  if (cur >= 0) flush_partials<V>(a, s, cur, acc);
   // last CTA to arrive reduces every CTA's partials in a fixed order
   __threadfence();
   __syncthreads();
