@@ -86,6 +86,8 @@ struct ftlm_system {
   DevBuf Vs, Wc, Od;     // symmetric runs: stored Lanczos vectors, u.S chunk, O matrices
   DevBuf Gre;            // re-orthogonalised runs: <q_k|w_r> coefficients [R][M] complex
   DevBuf Ta, Tb;         // ftlm_apply_h on spin-1/2 blocks: x and H x in the vector-major layout
+  DevBuf ut[2];          // per-unit coefficient tables of the one-pass vector-major gather, [c64]
+  int ut_K[2] = {0, 0};  // the cube size each was built for
   cudaEvent_t ev_apply = nullptr;  // recorded after the last use of Ta, Tb
   bool apply_used = false;
   std::mutex mu;
@@ -447,6 +449,25 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
 // the step's w' in its epilogue, then the update pass (see enqueue_run).
 bool vm_fused_step(const Plan& pl) { return pl.half.on && pl.half.vm && pl.half.passes == 1 && !pl.half.hybrid; }
 
+// The per-unit coefficient tables of the one-pass vector-major gather with K
+// cube bits, built once per system (and rebuilt for another K or precision)
+// on stream st; their pointer is baked into captured graphs, so a rebuild
+// bumps the system's generation.
+ftlm_status ensure_unit_tables(ftlm_system* s, int K, int c64, cudaStream_t st) {
+  DevBuf& b = s->ut[c64 ? 1 : 0];
+  if (b.p && s->ut_K[c64 ? 1 : 0] == K) return FTLM_OK;
+  const int n = s->hs.n;
+  const long long nunits = (long long)(s->hs.dim >> (kVmLaneBits + K));
+  const size_t bytes = (size_t)nunits * vm_unit_table_stride(n, K) * (c64 ? 4 : 8);
+  if (b.p) CK(cudaDeviceSynchronize());  // a rebuild: no launch may still read the old tables
+  b.release();
+  CK(b.ensure(bytes));
+  CKI(launch_vm_unit_tables(reinterpret_cast<const double*>(s->tab_d.p), s->hs.lay, n, K, nunits, b.p, c64, st));
+  s->ut_K[c64 ? 1 : 0] = K;
+  s->gen++;
+  return FTLM_OK;
+}
+
 int plan_max_grid(const Plan& pl) {
   return std::max(pl.grid, pl.half.on ? std::max(pl.half.grid, pl.half.stream_grid) : 0);
 }
@@ -639,6 +660,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   a.tile_start = reinterpret_cast<const int*>(ctx.tiles.p);
   a.partials = reinterpret_cast<double*>(ctx.partials.p);
   a.counter = reinterpret_cast<unsigned*>(ctx.counter.p);
+  if (fused_step) a.unit_tab = sys[0]->ut[c64 ? 1 : 0].p;  // built by run_impl before the capture
   ctx.launches = 0;
   ctx.hv_launches = 0;
   const bool tk = p->time_kernels != 0;
@@ -909,6 +931,10 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     ps = make_plan(sys, R, c64, pl, nullptr, true);
   }
   if (ps != FTLM_OK) return ps;
+  if (vm_fused_step(pl)) {
+    ftlm_status ut = ensure_unit_tables(sys[0], pl.half.K, c64, st);
+    if (ut != FTLM_OK) return ut;
+  }
   if (pl.half.on && !vm_fused_step(pl)) {  // (the fused vector-major step keeps no H q block)
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
@@ -1202,8 +1228,11 @@ ftlm_status rows_entry(const ftlm_system* cs, int mode, const double* u, const v
       }
       cudaStream_t st = pick_stream(s, stream);
       if (s->apply_used) CK(cudaStreamWaitEvent(st, s->ev_apply, 0));
+      ftlm_status ut = ensure_unit_tables(s, vp.half.K, c64, st);
+      if (ut != FTLM_OK) return ut;
       CKI(launch_to_vector_major(x, s->Ta.p, (long long)s->hs.dim, nvec, c64, st));
       LaunchArgs a = vp.base;
+      a.unit_tab = s->ut[c64 ? 1 : 0].p;
       a.inline_one = 1;
       a.one = base_desc(s, c64);
       a.one.x = s->Ta.p;
@@ -1368,7 +1397,7 @@ void ftlm_system_destroy(ftlm_system* s) {
   cudaDeviceSynchronize();  // the system's buffers may be in use on any stream
   purge_ctx_of(s->id);
   for (DevBuf* b : {&s->tab_f, &s->tab_d, &s->stride, &s->q, &s->A, &s->B, &s->U, &s->scal, &s->ep, &s->ecnt,
-                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre, &s->Ta, &s->Tb})
+                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre, &s->Ta, &s->Tb, &s->ut[0], &s->ut[1]})
     b->release();
   cudaEventDestroy(s->ev_in);
   cudaEventDestroy(s->ev_out);

@@ -168,6 +168,9 @@ struct LaunchArgs {
   // Re<q_j|w'> and <q_j|u>; its last CTA sets alpha_j and p_j.  The rest of
   // the step, w = w' - alpha_j sigma_j q_j with |w|^2, is kModeUpdate.
   int fused_step = 0;
+  // vector-major one-pass gather: the system's per-unit coefficient tables
+  // (launch_vm_unit_tables), or nullptr to build them in the kernel
+  const void* unit_tab = nullptr;
 };
 
 // Launch shapes chosen per (path, R, dtype); see autotuning in api.cu.
@@ -225,6 +228,11 @@ size_t vm_smem_bytes(int n, int K, int threads, int npass, int c64);
 int set_vm_carveout(int K, int c64, bool multipass, int min_blocks, size_t smem, int ctas);
 int prepare_vm_kernels(size_t smem);
 int vm_max_ctas_per_sm(int K, int min_blocks, int c64, int threads, size_t smem, bool multipass);
+// per-unit coefficient tables of the one-pass form: stride reals a unit,
+// d >> (5 + K) units, computed from the FP64 coupling tables
+int vm_unit_table_stride(int n, int K);
+int launch_vm_unit_tables(const double* tab_d, const TabLayout& L, int n, int K, long long nunits, void* out, int c64,
+                          void* stream);
 // kModeStep / kModeStartNorm over the same one-vector instances (256 threads)
 int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream);
 constexpr int kVmLaneBits = 5;  // rows per warp-wide load: 2^5

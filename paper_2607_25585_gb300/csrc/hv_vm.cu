@@ -98,6 +98,49 @@ __device__ __forceinline__ real zzc(const real* t, const TabLayout& L, int n, in
   return i < j ? t[L.off_zz + i * n + j] : t[L.off_zz + j * n + i];
 }
 
+__host__ __device__ constexpr int ctz_const(int x) {
+  int c = 0;
+  while (!(x & 1)) {
+    x >>= 1;
+    ++c;
+  }
+  return c;
+}
+
+// The cube-dependent part of site j's single-flip coefficient,
+// fc(r) = sum_c rho_{j, cube bit c} m_c(r), for the 2^K cube rows r in
+// Gray-code order (consecutive rows differ in one bit c, so fc changes by
+// +-rho_c): f(r, fc(r)) for every r, from 1 + K shared-memory reads of the
+// table fcp_j[r] (rows 0 and 2^c) instead of 2^K.
+template <typename real, int K, typename F>
+__device__ __forceinline__ void gray_fc(const real* fcp_j, F&& f) {
+  using v2 = typename Cx<real>::v2;
+  constexpr int NR = 1 << K;
+  const v2 f0 = *reinterpret_cast<const v2*>(fcp_j);
+  v2 rho[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    const v2 fb = *reinterpret_cast<const v2*>(fcp_j + 2 * (1 << c));
+    rho[c].x = fb.x - f0.x;
+    rho[c].y = fb.y - f0.y;
+  }
+  v2 v = f0;
+#pragma unroll
+  for (int g = 0; g < NR; ++g) {
+    f(g ^ (g >> 1), v);
+    if (g + 1 < NR) {
+      const int c = ctz_const(g + 1);
+      if ((((g + 1) ^ ((g + 1) >> 1)) >> c) & 1) {
+        v.x += rho[c].x;
+        v.y += rho[c].y;
+      } else {
+        v.x -= rho[c].x;
+        v.y -= rho[c].y;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // Dynamic shared memory of vm_kernel (tables of `real`: 4 bytes for
@@ -341,9 +384,16 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
       const unsigned long long u = (unsigned long long)(unit0 + ui);
       if ((long long)u >= nunits) break;
       const unsigned long long base = ((u >> (s0 - CB)) << (s0 + K)) | ((u & lowmask) << CB);
-      // unit tables (the outer bits' share of the coefficients), the warp's lanes in parallel
+      // unit tables (the outer bits' share of the coefficients): copied from the
+      // system's precomputed per-unit tables (one-pass form), or built by the
+      // warp's lanes in parallel
       __syncwarp();
-      for (int j = lane; j < n; j += 32) {
+      const bool from_table = !MP && a.hybrid == 0 && a.unit_tab != nullptr;
+      if (from_table) {
+        const real* src = reinterpret_cast<const real*>(a.unit_tab) + (size_t)u * wstride;
+        for (int k = lane; k < wstride; k += 32) W[k] = src[k];
+      }
+      for (int j = lane; j < n && !from_table; j += 32) {
         real fr = t[L.off_hp + 2 * j], fi = t[L.off_hp + 2 * j + 1];
         for (int i = CB; i < n; ++i) {
           if (in_cube(i)) continue;
@@ -354,7 +404,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
         fs[2 * j] = fr;
         fs[2 * j + 1] = fi;
       }
-      if (first) {
+      if (first && !from_table) {
         if (lane < CB) {  // lane bit `lane` x outer bits
           real h = 0;
           for (int j = CB; j < n; ++j)
@@ -435,12 +485,19 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
         const v2 f0 = ld2(fs + 2 * sc), f1 = ld2(S.fl + 2 * (sc * 32 + lane));
         const real br = om * (f0.x + f1.x);
         const real bi = om * (f0.y + f1.y);
+        if (!MP) {
+          gray_fc<real, K>(fcp + 2 * (sc * NR), [&](int r, const v2 fc) {
+            const real fim = bi + fc.y;
+            acc[r].mac(br + fc.x, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
+          });
+        } else {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const v2 fc = ld2(fcp + 2 * (sc * NR + r));
-          const real fr = br + fc.x;
-          const real fim = bi + fc.y;
-          acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
+          for (int r = 0; r < NR; ++r) {
+            const v2 fc = ld2(fcp + 2 * (sc * NR + r));
+            const real fr = br + fc.x;
+            const real fim = bi + fc.y;
+            acc[r].mac(fr, ((r >> c) & 1) ? fim : -fim, xo[r ^ (1 << c)]);
+          }
         }
 #pragma unroll
         for (int c1 = 0; c1 < c; ++c1) {
@@ -466,11 +523,18 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) vm_kernel(const _
         if (first && j < single_hi) {
           const v2 f0 = ld2(fs + 2 * j), f1 = ld2(S.fl + 2 * (j * 32 + lane));
           const real br = f0.x + f1.x, bi = f0.y + f1.y;
+          if (!MP) {
+            gray_fc<real, K>(fcp + 2 * (j * NR), [&](int r, const v2 fc) {
+              const real fim = bi + fc.y;
+              acc[r].mac(br + fc.x, bj ? fim : -fim, yv[r]);
+            });
+          } else {
 #pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            const v2 fc = ld2(fcp + 2 * (j * NR + r));
-            const real fim = bi + fc.y;
-            acc[r].mac(br + fc.x, bj ? fim : -fim, yv[r]);
+            for (int r = 0; r < NR; ++r) {
+              const v2 fc = ld2(fcp + 2 * (j * NR + r));
+              const real fim = bi + fc.y;
+              acc[r].mac(br + fc.x, bj ? fim : -fim, yv[r]);
+            }
           }
         }
         const bool uniform = j >= CB;  // bit j (not a lane bit) is the same for the whole warp
@@ -691,6 +755,65 @@ __global__ void __launch_bounds__(256) vm_stream_kernel(const __grid_constant__ 
   __threadfence();
   finalize(a, a.inst);
   if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// The per-unit tables of the one-pass vector-major gather (cube on bits
+// [5, 5 + K), outer bits [5 + K, n)): for unit u (outer bits = the bits of u),
+// the warp table [fs (2n) | hs (5) | gs (K) | es (1) | pad], stride reals a
+// unit, with the definitions the gather uses when it builds them itself:
+//   fs_j = h+_j + sum_{i outer} rho_ji m_i,   hs_l = sum_{j outer} zz_lj m_j,
+//   gs_c = sum_{i outer} zz_{5+c, i} m_i,
+//   es = sum_{i outer} (m_i (hz_i + sum_{j > i outer} zz_ij m_j) + iondiag_i(b_i)),
+// evaluated in FP64 from the FP64 coupling tables, one thread per unit.
+template <typename real>
+__global__ void vm_unit_tables_kernel(const double* __restrict__ t, const TabLayout L, int n, int K, long long nunits,
+                                      int stride, real* __restrict__ out) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nunits) return;
+  const int lo = kLaneBits + K;
+  const unsigned long long base = (unsigned long long)u << lo;
+  auto m = [&](int i) { return ((base >> i) & 1ull) ? 0.5 : -0.5; };
+  auto zz = [&](int i, int j) { return i < j ? t[L.off_zz + i * n + j] : t[L.off_zz + j * n + i]; };
+  real* o = out + (size_t)u * stride;
+  for (int j = 0; j < n; ++j) {
+    double fr = t[L.off_hp + 2 * j], fi = t[L.off_hp + 2 * j + 1];
+    for (int i = lo; i < n; ++i) {
+      fr += t[L.off_rho + 2 * (j * n + i)] * m(i);
+      fi += t[L.off_rho + 2 * (j * n + i) + 1] * m(i);
+    }
+    o[2 * j] = (real)fr;
+    o[2 * j + 1] = (real)fi;
+  }
+  for (int l = 0; l < kLaneBits; ++l) {
+    double h = 0.0;
+    for (int j = lo; j < n; ++j) h += zz(l, j) * m(j);
+    o[2 * n + l] = (real)h;
+  }
+  for (int c = 0; c < K; ++c) {
+    double g = 0.0;
+    for (int i = lo; i < n; ++i) g += zz(kLaneBits + c, i) * m(i);
+    o[2 * n + kLaneBits + c] = (real)g;
+  }
+  double e = 0.0;
+  for (int i = lo; i < n; ++i) {
+    double zs = t[L.off_hz + i];
+    for (int j = i + 1; j < n; ++j) zs += zz(i, j) * m(j);
+    e += m(i) * zs + t[L.off_iondiag + i * L.qmax + (int)((base >> i) & 1ull)];
+  }
+  o[2 * n + kLaneBits + K] = (real)e;
+  for (int k = 2 * n + kLaneBits + K + 1; k < stride; ++k) o[k] = (real)0;
+}
+
+int vm_unit_table_stride(int n, int K) { return (2 * n + kLaneBits + K + 1 + 1) & ~1; }
+
+int launch_vm_unit_tables(const double* tab_d, const TabLayout& L, int n, int K, long long nunits, void* out, int c64,
+                          void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int stride = vm_unit_table_stride(n, K);
+  const unsigned grid = (unsigned)((nunits + 127) / 128);
+  if (c64) vm_unit_tables_kernel<float><<<grid, 128, 0, st>>>(tab_d, L, n, K, nunits, stride, (float*)out);
+  else vm_unit_tables_kernel<double><<<grid, 128, 0, st>>>(tab_d, L, n, K, nunits, stride, (double*)out);
+  return (int)cudaGetLastError();
 }
 
 int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream) {
