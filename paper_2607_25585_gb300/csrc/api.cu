@@ -181,7 +181,17 @@ struct Plan {
   std::vector<int> tile_start;
   HalfPlan half;  // spin-1/2 kernel for the H.v modes, when applicable
   int wideV = 0;  // general kernel: H.v with 4 or 8 complex64 vectors per thread (0 = off)
+  // vector-major general plan (any spins, several systems): every vector of a
+  // run contiguous; the streaming modes see one instance per (system, vector),
+  // H.v runs rows_vm_kernel over groups of gvm_V vectors of one system
+  bool gen_vm = false;
+  int gvm_V = 1, gvm_groups = 0, gvm_ntiles = 0, gvm_rows = 0, gvm_grid = 0;
+  size_t gvm_smem = 0;
+  std::vector<int> tile_start_g;  // prefix sum of H.v tiles over the groups
 };
+
+// the run keeps each Lanczos vector contiguous
+bool plan_vmaj(const Plan& pl) { return pl.half.vm || pl.gen_vm; }
 
 int largest_divisor_at_most(int R, int cap) {
   for (int g = std::min(R, cap); g >= 1; --g)
@@ -353,6 +363,40 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
       return gs;
     }
   }
+  if (allow_vm && !force && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
+    // default for runs on other systems and batches: the vector-major general gather
+    int V = 1;
+    for (int v : {8, 4, 2, 1})
+      if (R % v == 0 && rows_vm_supported(v, c64)) {
+        V = v;
+        break;
+      }
+    std::vector<ftlm_system*> vecs;  // one instance per (system, vector), system-major
+    for (auto* s : sys)
+      for (int k = 0; k < R; ++k) vecs.push_back(s);
+    const Shape keep = pl.sh;
+    pl.sh = default_shape(1, c64);
+    ftlm_status gs = make_general(vecs, 1, c64, pl);
+    if (gs != FTLM_OK) return gs;
+    pl.sh.half_K = keep.half_K;
+    pl.gen_vm = true;
+    pl.gvm_V = V;
+    pl.gvm_rows = 1024;  // four rows a thread of a 256-thread CTA
+    pl.tile_start_g.assign(1, 0);
+    for (auto* s : sys)
+      for (int g = 0; g < R / V; ++g) {
+        const long long tiles = ((long long)s->hs.dim + pl.gvm_rows - 1) / pl.gvm_rows;
+        if (pl.tile_start_g.back() + tiles > (1ll << 30)) return fail(FTLM_ERR_UNSUPPORTED, "too many tiles");
+        pl.tile_start_g.push_back(pl.tile_start_g.back() + (int)tiles);
+      }
+    pl.gvm_groups = (int)pl.tile_start_g.size() - 1;
+    pl.gvm_ntiles = pl.tile_start_g.back();
+    pl.gvm_smem = pl.smem;  // the same tables and per-thread columns as the streaming plan
+    CKI(prepare_rows_vm(V, c64, std::max<size_t>(pl.gvm_smem, 48 * 1024)));
+    const int per_sm = rows_vm_ctas_per_sm(V, c64, 256, pl.gvm_smem);
+    pl.gvm_grid = std::max(1, std::min(pl.gvm_ntiles, std::max(1, device_sm_count()) * per_sm));
+    return FTLM_OK;
+  }
   ftlm_status gs = make_general(sys, R, c64, pl);
   if (gs != FTLM_OK) return gs;
   if (sys.size() == 1 && pl.sh.half_K > 0 && !pl.sh.half_vm)
@@ -366,6 +410,13 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
 // Launches one mode of the plan: the spin-1/2 kernel for H.v modes when the
 // plan has it, the general row kernel otherwise.
 int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
+  if (pl.gen_vm && a.mode == kModeApply) {  // the groups' tile list follows the instances' in the same buffer
+    a.n_inst = pl.gvm_groups;
+    a.ntiles = pl.gvm_ntiles;
+    a.rows_per_tile = pl.gvm_rows;
+    if (!a.inline_one) a.tile_start += pl.base.n_inst + 1;
+    return launch_rows_vm(a, pl.gvm_V, pl.c64, pl.gvm_grid, 256, pl.gvm_smem, st);
+  }
   if (pl.half.on && pl.half.vm && (a.mode == kModeStep || a.mode == kModeStartNorm || a.mode == kModeUpdate)) {
     a.rows_per_tile = pl.half.stream_rows;
     a.tiles_per_vg = pl.half.stream_tiles_per_vg;
@@ -469,7 +520,8 @@ ftlm_status ensure_unit_tables(ftlm_system* s, int K, int c64, cudaStream_t st) 
 }
 
 int plan_max_grid(const Plan& pl) {
-  return std::max(pl.grid, pl.half.on ? std::max(pl.half.grid, pl.half.stream_grid) : 0);
+  return std::max(std::max(pl.grid, pl.gen_vm ? pl.gvm_grid : 0),
+                  pl.half.on ? std::max(pl.half.grid, pl.half.stream_grid) : 0);
 }
 
 // ---- workspace ----------------------------------------------------------------
@@ -592,6 +644,7 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
   k += buf;
   k += p->symmetric ? "|sym" : "";
   k += p->reorth ? "|reorth" : "";
+  k += pl.gen_vm ? "|gvm" + std::to_string(pl.gvm_V) : "";
   snprintf(buf, sizeof buf, "|half%d vm%d hy%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
            pl.half.hybrid ? 1 : 0,
            pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
@@ -642,14 +695,14 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
                         cudaStream_t st) {
   const int M = p->M, R = p->R, c64 = pl.c64;
   const int n = (int)sys.size();
-  const int nd = pl.half.vm ? R : n;  // descriptors per kind: one per vector in the vector-major layout
+  const int nd = plan_vmaj(pl) ? n * R : n;  // descriptors per kind: one per (system, vector) in the vector-major layout
   const InstDesc* d_even = reinterpret_cast<const InstDesc*>(ctx.desc.p);
   const InstDesc* d_odd = d_even + nd;
   const InstDesc* d_start = d_even + 2 * nd;
   const InstDesc* d_gather_even = d_even + 3 * nd;  // split steps: x = q_j, y = Hq
   const InstDesc* d_gather_odd = d_even + 4 * nd;
   // the spin-1/2 gathers and the wide general gather run alone; the step epilogue streams afterwards
-  const bool split = pl.half.on || pl.wideV;
+  const bool split = pl.half.on || pl.wideV || pl.gen_vm;
   // single-pass gathers also sum Re<q_j|H q_j>, so alpha_j is known before the
   // epilogue, which then finishes the step in one pass (no separate update)
   const bool fused = pl.half.on && (pl.half.passes == 1 || pl.half.vm);
@@ -666,7 +719,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
   const bool tk = p->time_kernels != 0;
   int evi = 0;
   if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
-  const int vmaj = pl.half.vm ? 1 : 0;
+  const int vmaj = plan_vmaj(pl) ? 1 : 0;
   for (int k = 0; k < n; ++k) {  // start block -> A
     InstDesc h = base_desc(sys[k], c64);
     const long long dim = (long long)sys[k]->hs.dim;
@@ -708,7 +761,7 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       const size_t vb = (size_t)s0->hs.dim * R * (c64 ? 8 : 16);
       const void* q = (j % 2 == 0) ? s0->A.p : s0->B.p;
       void* dst = static_cast<char*>(s0->Vs.p) + vb * j;
-      if (pl.half.vm) CK(cudaMemcpyAsync(dst, q, vb, cudaMemcpyDeviceToDevice, st));
+      if (plan_vmaj(pl)) CK(cudaMemcpyAsync(dst, q, vb, cudaMemcpyDeviceToDevice, st));
       else CKI(launch_to_vector_major(q, dst, (long long)s0->hs.dim, R, c64, st));
       ctx.launches++;
     }
@@ -792,13 +845,15 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
   // descriptors: even steps (x = A, y = B), odd steps (x = B, y = A), start (x = A, y = U),
   // and for split steps the gathers (x = A or B, y = Hq); one per system, or in the
   // vector-major layout one per vector (pointers at vector k, scalars of vector k)
-  const int nd = pl.half.vm ? R : n;
+  const bool vmaj = plan_vmaj(pl);
+  const int nd = vmaj ? n * R : n;
   std::vector<InstDesc> h(5 * nd);
   for (int k = 0; k < nd; ++k) {
-    ftlm_system* s = sys[pl.half.vm ? 0 : k];
+    ftlm_system* s = sys[vmaj ? k / R : k];  // vector-major: instance k is vector k % R of system k / R
+    const int vec = vmaj ? k % R : 0;
     InstDesc d = base_desc(s, c64);
-    d.sc = pl.half.vm ? scalars_of_vector(s->scal.p, R, M, k) : scalars_at(s->scal.p, R, M);
-    const size_t off = pl.half.vm ? (size_t)k * s->hs.dim * (c64 ? 8 : 16) : 0;  // bytes to vector k
+    d.sc = vmaj ? scalars_of_vector(s->scal.p, R, M, vec) : scalars_at(s->scal.p, R, M);
+    const size_t off = vmaj ? (size_t)vec * s->hs.dim * (c64 ? 8 : 16) : 0;  // bytes to vector vec
     char* A = static_cast<char*>(s->A.p) + off;
     char* B = static_cast<char*>(s->B.p) + off;
     char* U = static_cast<char*>(s->U.p) + off;
@@ -828,12 +883,14 @@ ftlm_status build_ctx(RunCtx& c, const std::vector<ftlm_system*>& sys, const ftl
   }
   CK(c.desc.ensure(sizeof(InstDesc) * h.size()));
   CK(cudaMemcpy(c.desc.p, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice));
-  CK(c.tiles.ensure(sizeof(int) * pl.tile_start.size()));
-  CK(cudaMemcpy(c.tiles.p, pl.tile_start.data(), sizeof(int) * pl.tile_start.size(), cudaMemcpyHostToDevice));
+  std::vector<int> tiles = pl.tile_start;  // the instances' tile list, then the H.v groups' (vector-major general)
+  tiles.insert(tiles.end(), pl.tile_start_g.begin(), pl.tile_start_g.end());
+  CK(c.tiles.ensure(sizeof(int) * tiles.size()));
+  CK(cudaMemcpy(c.tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice));
   CK(c.partials.ensure(sizeof(double) * (size_t)n * plan_max_grid(pl) * R * kNumPartials));  // n_inst x R = R x 1 when vector-major
   CK(c.counter.ensure(64));
   CK(cudaMemset(c.counter.p, 0, 64));
-  c.h2d = sizeof(InstDesc) * h.size() + sizeof(int) * pl.tile_start.size();
+  c.h2d = sizeof(InstDesc) * h.size() + sizeof(int) * tiles.size();
   CK(cudaMallocHost(reinterpret_cast<void**>(&c.pinned), staged_bytes(R, M) * n));
   if (p->time_kernels) {
     c.ev.resize(4 * M + 2);
@@ -938,7 +995,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   if (pl.half.on && !vm_fused_step(pl)) {  // (the fused vector-major step keeps no H q block)
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
-  } else if (pl.wideV) {
+  } else if (pl.wideV || pl.gen_vm) {
     for (auto* s : sys) {
       ftlm_status hs_ = ensure_hq(s, R, c64, 1);
       if (hs_ != FTLM_OK) return hs_;
@@ -1040,13 +1097,13 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     out.kernel_launches = ctx->launches;
     out.h2d_bytes = k == 0 ? h2d : 0;
     out.d2h_bytes = per;
-    out.cube_bits = pl.half.on ? pl.half.K : 0;
+    out.cube_bits = pl.half.on ? pl.half.K : 0;  // (0 also for the vector-major general gather)
     out.passes = pl.half.on ? pl.half.passes : 1;
-    out.group_vectors = pl.half.on ? pl.half.Rg : R;
-    out.tile_rows = pl.half.on ? pl.half.rows_per_tile : pl.sh.rows_per_tile;
-    out.grid = pl.half.on ? pl.half.grid : pl.grid;
-    out.threads = pl.half.on ? pl.half.threads : pl.sh.threads;
-    out.vector_major = pl.half.vm ? 1 : 0;
+    out.group_vectors = pl.half.on ? pl.half.Rg : (pl.gen_vm ? pl.gvm_V : R);
+    out.tile_rows = pl.half.on ? pl.half.rows_per_tile : (pl.gen_vm ? pl.gvm_rows : pl.sh.rows_per_tile);
+    out.grid = pl.half.on ? pl.half.grid : (pl.gen_vm ? pl.gvm_grid : pl.grid);
+    out.threads = pl.half.on ? pl.half.threads : (pl.gen_vm ? 256 : pl.sh.threads);
+    out.vector_major = plan_vmaj(pl) ? 1 : 0;
     out.sym_ms = 0.0;
     if (p->symmetric) {  // Eqs. (E-2-G), (E-2-H)
       const double* sigma_d = p_d + (size_t)M * R * 2;  // [M][R]

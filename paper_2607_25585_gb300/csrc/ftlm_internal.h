@@ -209,6 +209,11 @@ int launch_rows_wide(const LaunchArgs& a, int V, int grid, int threads, size_t s
 int prepare_rows_kernels(size_t smem);
 // CTAs per SM of the Lanczos-mode row kernel, or of the wide H.v kernel when wideV is 4 or 8
 int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int wideV);
+// vector-major general H.v: V vectors a thread (c64: 1, 2, 4, 8; c128: 1, 2, 4)
+int rows_vm_supported(int V, int c64);
+int prepare_rows_vm(int V, int c64, size_t smem);
+int rows_vm_ctas_per_sm(int V, int c64, int threads, size_t smem);
+int launch_rows_vm(const LaunchArgs& a, int V, int c64, int grid, int threads, size_t smem, void* stream);
 int device_sm_count();
 long long device_l2_bytes();
 

@@ -288,6 +288,89 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
 }
 
 // ---------------------------------------------------------------------------
+// the vector-major general H.v
+// ---------------------------------------------------------------------------
+// The gather of row_terms against V vectors of one system that lie dim
+// elements apart (each vector contiguous): a warp's 32 lanes own 32
+// consecutive rows, so every load of a term is 32 consecutive values of one
+// vector (one 256-byte line pair), and the row's matrix elements are formed
+// once for its V vectors.
+template <typename real, int V>
+struct VmGatherSink {
+  using v2 = typename Cx<real>::v2;
+  const v2* x;    // vector 0 of the group
+  long long mu;   // the row
+  long long vs;   // elements from one vector of the group to the next
+  real *ar, *ai;
+  __device__ __forceinline__ void diag(real dv) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const v2 xv = __ldg(x + v * vs + mu);
+      ar[v] = dv * xv.x;
+      ai[v] = dv * xv.y;
+    }
+  }
+  __device__ __forceinline__ void term(long long nu, real cr, real ci) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const v2 xv = __ldg(x + v * vs + nu);
+      ar[v] = fma(cr, xv.x, ar[v]);
+      ar[v] = fma(-ci, xv.y, ar[v]);
+      ai[v] = fma(cr, xv.y, ai[v]);
+      ai[v] = fma(ci, xv.x, ai[v]);
+    }
+  }
+};
+
+// y = H x on vector-major blocks.  a.inst holds one descriptor per vector
+// (one-vector instances, the V vectors of a group consecutive and dim apart);
+// a.tile_start is the prefix sum of tiles over the groups (a.n_inst groups),
+// a tile being a.rows_per_tile rows of one group.  Tiles go round-robin over
+// the CTAs, so CTAs running together share a group's neighbourhood in L2.
+template <typename real, int V>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2) rows_vm_kernel(const __grid_constant__ LaunchArgs a) {
+  using v2 = typename Cx<real>::v2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SmemView s = carve<real>(smem_raw, a, 0);
+  __shared__ InstDesc d;
+  const InstDesc* insts = a.inline_one ? &a.one : a.inst;
+  int cur = -1;
+  const void* staged = nullptr;  // tables of the system now in shared memory
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int g = a.inline_one ? 0 : find_instance(a.tile_start, a.n_inst, tile);
+    if (g != cur) {
+      __syncthreads();
+      if (threadIdx.x == 0) d = insts[(size_t)g * V];
+      __syncthreads();
+      if (d.tab != staged) {  // the groups of one system share its tables
+        stage_instance<real>(d, s);
+        staged = d.tab;
+      }
+      cur = g;
+      __syncthreads();
+    }
+    const int first_tile = a.inline_one ? 0 : __ldg(a.tile_start + g);
+    const long long row0 = (long long)(tile - first_tile) * a.rows_per_tile;
+    const long long row_end = min(row0 + a.rows_per_tile, d.dim);
+    const bool idx32 = d.dim <= 0xffffffffll;
+    const v2* x = reinterpret_cast<const v2*>(d.x);
+    v2* y = reinterpret_cast<v2*>(d.y);
+    for (long long mu = row0 + threadIdx.x; mu < row_end; mu += blockDim.x) {
+      real ar[V], ai[V];
+      VmGatherSink<real, V> sink{x, mu, d.dim, ar, ai};
+      row_terms<real>(s, d.lay, d.n, mu, idx32, sink);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        v2 o;
+        o.x = ar[v];
+        o.y = ai[v];
+        y[v * d.dim + mu] = o;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // start vectors: Philox4x32-10 (Salmon et al., SC'11), Box-Muller in FP64
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void philox_round(unsigned& c0, unsigned& c1, unsigned& c2, unsigned& c3, unsigned k0,
@@ -509,6 +592,58 @@ int launch_rows(const LaunchArgs& a, int c64, int grid, int threads, size_t smem
     return launch_mode<float, 1>(a, grid, threads, smem, st);
   }
   return launch_mode<double, 1>(a, grid, threads, smem, st);
+}
+
+template <typename real, int V>
+static const void* rows_vm_fn() {
+  return (const void*)rows_vm_kernel<real, V>;
+}
+
+static const void* rows_vm_pick(int V, int c64) {
+  if (c64) {
+    if (V == 8) return rows_vm_fn<float, 8>();
+    if (V == 4) return rows_vm_fn<float, 4>();
+    if (V == 2) return rows_vm_fn<float, 2>();
+    if (V == 1) return rows_vm_fn<float, 1>();
+  } else {
+    if (V == 4) return rows_vm_fn<double, 4>();
+    if (V == 2) return rows_vm_fn<double, 2>();
+    if (V == 1) return rows_vm_fn<double, 1>();
+  }
+  return nullptr;
+}
+
+int rows_vm_supported(int V, int c64) { return rows_vm_pick(V, c64) != nullptr; }
+
+int prepare_rows_vm(int V, int c64, size_t smem) {
+  const void* k = rows_vm_pick(V, c64);
+  if (!k) return (int)cudaErrorInvalidValue;
+  return (int)cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int rows_vm_ctas_per_sm(int V, int c64, int threads, size_t smem) {
+  const void* k = rows_vm_pick(V, c64);
+  int n = 0;
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+int launch_rows_vm(const LaunchArgs& a, int V, int c64, int grid, int threads, size_t smem, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (a.mode != kModeApply) return (int)cudaErrorInvalidValue;
+  if (c64) {
+    if (V == 8) rows_vm_kernel<float, 8><<<grid, threads, smem, st>>>(a);
+    else if (V == 4) rows_vm_kernel<float, 4><<<grid, threads, smem, st>>>(a);
+    else if (V == 2) rows_vm_kernel<float, 2><<<grid, threads, smem, st>>>(a);
+    else if (V == 1) rows_vm_kernel<float, 1><<<grid, threads, smem, st>>>(a);
+    else return (int)cudaErrorInvalidValue;
+  } else {
+    if (V == 4) rows_vm_kernel<double, 4><<<grid, threads, smem, st>>>(a);
+    else if (V == 2) rows_vm_kernel<double, 2><<<grid, threads, smem, st>>>(a);
+    else if (V == 1) rows_vm_kernel<double, 1><<<grid, threads, smem, st>>>(a);
+    else return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
 }
 
 int rows_max_ctas_per_sm(int c64, int threads, size_t smem, int wideV) {
