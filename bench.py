@@ -45,16 +45,47 @@ def load_peaks():
         return {}
 
 
-def algorithmic_flops_per_sv(two_s, lattice_half=True):
-    """Flops one state x vector needs per Lanczos step in the matvec, for
-    s = 1/2: every pair flip is a complex multiply-add (8 flops) except the
-    s+ s- / s- s+ terms, whose coefficient is real (4 flops) and which occur
-    for half of the pairs on average; every single-site flip is complex
-    (8 flops); the diagonal is real (2 flops); the fused epilogue (the
-    beta term, alpha and p reductions) adds 14."""
-    n = len(two_s)
-    pairs = n * (n - 1) // 2
-    return pairs * 0.5 * (4 + 8) + n * 8 + 2 + 14
+def algorithmic_flops_per_sv(two_s, epilogue=True):
+    """Flops one state x vector needs per Lanczos step in the matvec, averaged
+    over the product basis (site i has q_i = 2 s_i + 1 levels; a raising flip
+    is possible from q_i - 1 of them, a double flip from q_i - 2): a pair's
+    s+ s- / s- s+ terms have a real coefficient (4 flops each), its s+ s+ /
+    s- s- terms a complex one (8 flops); every single-site flip by one or two
+    levels is complex (8 flops); the diagonal is real (2 flops); the fused
+    epilogue (the beta term, alpha and p reductions) adds 14.  For s = 1/2
+    every pair has exactly one possible flip: 6 flops on average."""
+    q = np.asarray(two_s, dtype=np.float64) + 1.0
+    up = (q - 1.0) / q            # P(a site can be raised) = P(it can be lowered)
+    up2 = np.maximum(q - 2.0, 0.0) / q
+    flops = 2.0 + (14.0 if epilogue else 0.0)
+    n = len(q)
+    for i in range(n):
+        flops += 8.0 * 2.0 * up[i] + 8.0 * 2.0 * up2[i]
+        for j in range(i + 1, n):
+            flops += 4.0 * 2.0 * up[i] * up[j] + 8.0 * 2.0 * up[i] * up[j]
+    return float(flops)
+
+
+def gather_kernel_name(shp):
+    """The H.v kernel a launch shape names."""
+    if shp.get("vector_major") and shp.get("cube_bits", 0) > 0:
+        return f"vm_kernel<float,{shp['cube_bits']}> (vector-major spin-1/2 gather)"
+    if shp.get("vector_major"):
+        return f"rows_vm_kernel<float,{shp['group_vectors']}> (vector-major general gather)"
+    if shp.get("cube_bits", 0) > 0:
+        return f"half_kernel<float,{shp['cube_bits']}> (row-major spin-1/2 register-cube gather)"
+    return "rows_kernel (row-major general gather)"
+
+
+def batch_roofline(systems_two_s, dims, R, hv_ms, sm_max_mhz, kernel):
+    """FP32 roofline of one H.v launch over a batch (the general gathers carry
+    no Lanczos epilogue: the step runs in the next launch)."""
+    flops = sum(algorithmic_flops_per_sv(t, epilogue=False) * d * R for t, d in zip(systems_two_s, dims))
+    achieved = flops / (hv_ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_launch": flops, "hv_ms_per_launch": hv_ms,
+            "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"}
 
 
 class ClockSampler:
@@ -357,7 +388,8 @@ def extra_workloads(F, T, stream, args):
     import torch
     out = {}
     spec = W.WORKLOADS["chains_s1_x24"]
-    systems = [F.System.from_dict(w) for w in spec["system"]()]
+    ws_ = spec["system"]()
+    systems = [F.System.from_dict(w) for w in ws_]
     R, M = spec["R"], spec["M"]
     kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True)
     F.run_batch(systems, autotune=True, **kw)  # the autotuner picks the launch shape (kept for the timed run)
@@ -374,6 +406,10 @@ def extra_workloads(F, T, stream, args):
                             "launch_gap_ms_per_step": res[0]["gap_ms"] / max(1, M - 1),
                             "launch_gap_share": res[0]["gap_ms"] / max(1e-9, res[0]["device_ms"]),
                             "launch_shape": res[0]["shape"], "autotuned": True,
+                            "roofline": batch_roofline([w["two_s"] for w in ws_], [s.dim for s in systems], R,
+                                                       res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
+                                                       load_peaks().get("sm_max_mhz", 2070.0),
+                                                       gather_kernel_name(res[0]["shape"])),
                             "note": "one graph for all 24 instances; shape chosen by the autotuner"}
     for s in systems:
         s.close()
@@ -477,7 +513,8 @@ def mn9_leg(F, T, stream, args):
     start pairs; the powder average of M_B is over the 10 results."""
     import torch
     spec = W.WORKLOADS["mn9_powder"]
-    systems = [F.System.from_dict(w) for w in spec["system"]()]
+    ws_ = spec["system"]()
+    systems = [F.System.from_dict(w) for w in ws_]
     R, M = spec["R"], spec["M"]
     kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream, time_kernels=True, start="pairs")
     F.run_batch(systems, autotune=args.autotune, **kw)
@@ -491,10 +528,13 @@ def mn9_leg(F, T, stream, args):
     sv = sum(s.dim for s in systems) * R * M
     d = int(systems[0].dim)
     mb = np.mean([r["M_B"] for r in res], axis=0)
+    hv = res[0]["hv_ms"] / max(1, res[0]["hv_launches"])
+    roof = batch_roofline([w["two_s"] for w in ws_], [s.dim for s in systems], R, hv,
+                          load_peaks().get("sm_max_mhz", 2070.0), gather_kernel_name(res[0]["shape"]))
     for s in systems:
         s.close()
     return {"value": sv / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R, "directions": len(systems),
-            "d": d, "hv_ms_per_launch": res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
+            "d": d, "hv_ms_per_launch": hv, "roofline": roof,
             "launch_shape": res[0]["shape"], "powder_M_B_at_T": {f"{T[i]:.3g}": float(mb[i]) for i in (0, 20, 39)},
             "note": "one graph for the 10 directions; general mixed-radix kernel"}
 

@@ -83,7 +83,8 @@ struct ftlm_system {
   DevBuf A, B, U, scal;  // Lanczos workspace: two vector blocks, the observable block, scalars
   DevBuf Hq;             // H q_j when the gather and the step epilogue are separate launches
   DevBuf ep, ecnt, esc;  // start-block scratch: partials, arrival counter, scalars
-  DevBuf Vs, Wc, Od;     // symmetric runs: stored Lanczos vectors, u.S chunk, O matrices
+  DevBuf Vs, Wc, Od;     // symmetric runs: stored Lanczos vectors, partial sums of O, O matrices
+  DevBuf Ws;             // symmetric runs: u.S of the stored vectors (when it fits)
   DevBuf Gre;            // re-orthogonalised runs: <q_k|w_r> coefficients [R][M] complex
   DevBuf Ta, Tb;         // ftlm_apply_h on spin-1/2 blocks: x and H x in the vector-major layout
   DevBuf ut[2];          // per-unit coefficient tables of the one-pass vector-major gather, [c64]
@@ -363,8 +364,14 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
       return gs;
     }
   }
-  if (allow_vm && !force && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
-    // default for runs on other systems and batches: the vector-major general gather
+  // runs on other systems and batches: the vector-major general gather by
+  // default when the largest system's block of R vectors fits in L2 (measured
+  // on GB300: 24 % faster than the row-major gather on s = 1 chains whose
+  // largest block is 68 MB, 5 % slower on a 150 MB mixed-spin block), else
+  // the row-major one; an autotuned or forced shape decides for itself
+  const bool gvm_fits = (long long)big->hs.dim * R * (c64 ? 8 : 16) <= device_l2_bytes();
+  const bool want_gvm = pl.sh.general_vm == 1 || (pl.sh.general_vm < 0 && !force && gvm_fits);
+  if (allow_vm && want_gvm && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
     int V = 1;
     for (int v : {8, 4, 2, 1})
       if (R % v == 0 && rows_vm_supported(v, c64)) {
@@ -381,7 +388,7 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
     pl.sh.half_K = keep.half_K;
     pl.gen_vm = true;
     pl.gvm_V = V;
-    pl.gvm_rows = 1024;  // four rows a thread of a 256-thread CTA
+    pl.gvm_rows = keep.gvm_rows > 0 ? keep.gvm_rows : 1024;  // 1024: four rows a thread of a 256-thread CTA
     pl.tile_start_g.assign(1, 0);
     for (auto* s : sys)
       for (int g = 0; g < R / V; ++g) {
@@ -644,7 +651,7 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
   k += buf;
   k += p->symmetric ? "|sym" : "";
   k += p->reorth ? "|reorth" : "";
-  k += pl.gen_vm ? "|gvm" + std::to_string(pl.gvm_V) : "";
+  k += pl.gen_vm ? "|gvm" + std::to_string(pl.gvm_V) + "x" + std::to_string(pl.gvm_rows) : "";
   snprintf(buf, sizeof buf, "|half%d vm%d hy%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
            pl.half.hybrid ? 1 : 0,
            pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
@@ -932,13 +939,21 @@ ftlm_status symmetric_matrices(ftlm_system* s, const ftlm_run_params* p, cudaStr
     s->Od.release();
     if (s->Od.ensure(obytes) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "O matrices");
   }
+  // u.S q_k of all stored vectors beforehand when their copy fits (the size of
+  // the stored vectors); else the contraction forms them tile by tile
+  const size_t wbytes = (size_t)d * R * (c64 ? 8 : 16) * M;
+  if (s->Ws.bytes < wbytes) {
+    s->Ws.release();
+    if (s->Ws.ensure(wbytes) != cudaSuccess) cudaGetLastError();  // (a failed allocation leaves Ws empty)
+  }
+  void* W = s->Ws.bytes >= wbytes ? s->Ws.p : nullptr;
   InstDesc hd = base_desc(s, c64);
   observable_coefs(s->hs, p->obs_dir, hd.obs);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, st));
-  CKI(launch_sym_omat(&hd, s->Vs.p, R, M, nranges, reinterpret_cast<double*>(s->Wc.p),
+  CKI(launch_sym_omat(&hd, s->Vs.p, W, R, M, nranges, reinterpret_cast<double*>(s->Wc.p),
                       reinterpret_cast<double*>(s->Od.p), c64, st));
   CK(cudaEventRecord(e1, st));
   std::vector<double> host((size_t)R * M * M * 2);
@@ -1169,15 +1184,27 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
           }
   } else {
     for (int thr : {128, 256})
-      for (int f : {1, 4}) cands.push_back(shape_for(R, c64, thr, f));
+      for (int f : {1, 4}) {
+        Shape sh = shape_for(R, c64, thr, f);
+        sh.general_vm = 0;
+        cands.push_back(sh);
+      }
+    for (int rows : {512, 1024, 2048}) {  // the vector-major general gather (runs only)
+      Shape sh = default_shape(R, c64);
+      sh.general_vm = 1;
+      sh.gvm_rows = rows;
+      cands.push_back(sh);
+    }
   }
   ftlm_status w = ensure_workspace(s, R, 1, c64);
   if (w != FTLM_OK) return w;
   const size_t vbytes = (size_t)s->hs.dim * (c64 ? 8 : 16);
   CK(cudaMemsetAsync(s->A.p, 0, vbytes * R, st));
   DevBuf vdesc;  // the vector-major candidates: one descriptor per vector, output in Hq (one block per pass)
-  if (s->hs.all_half && s->hs.n >= kVmLaneBits + 3) {
-    ftlm_status hq = ensure_hq(s, R, c64, (s->hs.n - kVmLaneBits + 2) / 3);  // the most passes a candidate uses
+  DevBuf vtiles; // the vector-major general candidates' tile lists
+  if (!s->hs.all_half || s->hs.n >= kVmLaneBits + 3) {
+    const int passes = s->hs.all_half ? (s->hs.n - kVmLaneBits + 2) / 3 : 1;  // the most passes a candidate uses
+    ftlm_status hq = ensure_hq(s, R, c64, passes);
     if (hq != FTLM_OK) return hq;
     std::vector<InstDesc> h(R, base_desc(s, c64));
     for (int k = 0; k < R; ++k) {
@@ -1195,11 +1222,20 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
   std::vector<ftlm_system*> one{s};
   for (const Shape& sh : cands) {
     Plan pl;
-    if (make_plan(one, R, c64, pl, &sh, sh.half_vm != 0) != FTLM_OK) continue;
+    if (make_plan(one, R, c64, pl, &sh, sh.half_vm != 0 || sh.general_vm == 1) != FTLM_OK) continue;
     if (sh.half_K > 0 && (!pl.half.on || pl.half.vm != (sh.half_vm != 0))) continue;
+    if (sh.general_vm == 1 && !pl.gen_vm) continue;
     LaunchArgs a = pl.base;
     if (pl.half.vm) {
       a.inst = reinterpret_cast<const InstDesc*>(vdesc.p);
+    } else if (pl.gen_vm) {  // R one-vector instances, then the groups' tile list
+      std::vector<int> tiles = pl.tile_start;
+      tiles.insert(tiles.end(), pl.tile_start_g.begin(), pl.tile_start_g.end());
+      CK(cudaStreamSynchronize(st));  // (the previous candidate's launches may read the old list)
+      CK(vtiles.ensure(sizeof(int) * tiles.size()));
+      CK(cudaMemcpy(vtiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice));
+      a.inst = reinterpret_cast<const InstDesc*>(vdesc.p);
+      a.tile_start = reinterpret_cast<const int*>(vtiles.p);
     } else {
       a.inline_one = 1;
       a.one = base_desc(s, c64);
@@ -1223,6 +1259,8 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  vdesc.release();  // (every candidate's launches have completed: each ends with an event wait)
+  vtiles.release();
   std::lock_guard<std::mutex> lk(g_mu);
   g_shapes[key] = pick;
   return FTLM_OK;
@@ -1454,7 +1492,7 @@ void ftlm_system_destroy(ftlm_system* s) {
   cudaDeviceSynchronize();  // the system's buffers may be in use on any stream
   purge_ctx_of(s->id);
   for (DevBuf* b : {&s->tab_f, &s->tab_d, &s->stride, &s->q, &s->A, &s->B, &s->U, &s->scal, &s->ep, &s->ecnt,
-                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre, &s->Ta, &s->Tb, &s->ut[0], &s->ut[1]})
+                    &s->esc, &s->Hq, &s->Vs, &s->Wc, &s->Od, &s->Gre, &s->Ta, &s->Tb, &s->ut[0], &s->ut[1], &s->Ws})
     b->release();
   cudaEventDestroy(s->ev_in);
   cudaEventDestroy(s->ev_out);

@@ -225,6 +225,62 @@ __device__ __forceinline__ void update_stream(const InstDesc& d, long long e, lo
   }
 }
 
+// kModeEpilogue over the groups e, e + step, ... < e_end with U groups' loads
+// in flight per thread before their stores: w = sigma H q_j - beta sigma' q_{j-1}
+// in place of q_{j-1}, alpha and p partials (summed in the same group order
+// as one group at a time).
+template <typename real, int V, int U>
+__device__ __forceinline__ void epilogue_stream(const InstDesc& d, const LaunchArgs& a, long long e, long long e_end,
+                                                long long step, const real* sig, const real* bsp, real* pacc) {
+  auto finish = [&](long long idx, const real* ar, const real* ai, const real* xr, const real* xi, const real* qr,
+                    const real* qi, const real* ur, const real* ui) {
+    real wr[V], wi[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      wr[v] = a.first ? sig[v] * ar[v] : fma(sig[v], ar[v], -bsp[v] * qr[v]);
+      wi[v] = a.first ? sig[v] * ai[v] : fma(sig[v], ai[v], -bsp[v] * qi[v]);
+    }
+    VecIO<real, V>::st(d.y, idx, wr, wi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const real vr = sig[v] * xr[v], vi = sig[v] * xi[v];
+      pacc[v * kNumPartials + 0] += vr * wr[v] + vi * wi[v];
+      pacc[v * kNumPartials + 1] += vr * ur[v] + vi * ui[v];
+      pacc[v * kNumPartials + 2] += vr * ui[v] - vi * ur[v];
+    }
+  };
+  for (; e + (U - 1) * step < e_end; e += U * step) {
+    real ar[U][V], ai[U][V], xr[U][V], xi[U][V], qr[U][V], qi[U][V], ur[U][V], ui[U][V];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      VecIO<real, V>::ldg(d.hq, e + k * step, ar[k], ai[k]);
+      VecIO<real, V>::ldg(d.x, e + k * step, xr[k], xi[k]);
+      VecIO<real, V>::ldg(d.u, e + k * step, ur[k], ui[k]);
+      if (!a.first) {
+        VecIO<real, V>::ld(d.y, e + k * step, qr[k], qi[k]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) qr[k][v] = qi[k][v] = 0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) finish(e + k * step, ar[k], ai[k], xr[k], xi[k], qr[k], qi[k], ur[k], ui[k]);
+  }
+  for (; e < e_end; e += step) {
+    real ar[V], ai[V], xr[V], xi[V], qr[V], qi[V], ur[V], ui[V];
+    VecIO<real, V>::ldg(d.hq, e, ar, ai);
+    VecIO<real, V>::ldg(d.x, e, xr, xi);
+    VecIO<real, V>::ldg(d.u, e, ur, ui);
+    if (!a.first) {
+      VecIO<real, V>::ld(d.y, e, qr, qi);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) qr[v] = qi[v] = 0;
+    }
+    finish(e, ar, ai, xr, xi, qr, qi, ur, ui);
+  }
+}
+
 template <typename real, int V, int MODE>
 __device__ __forceinline__ void elementwise_item(const InstDesc& d, const LaunchArgs& a, long long idx,
                                                  const real* sig, const real* bsp, const real* coef, real* pacc) {

@@ -186,6 +186,8 @@ struct Shape {
   int half_vm = 0;         // spin-1/2 kernel: 1 = vector-major Lanczos block (ftlm_run only)
   int half_hybrid = 0;     // vector-major: the two-pass form (cubes on bits [5, 5+K) and the top K bits)
   bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
+  int general_vm = -1;     // general kernel in runs: 1 = vector-major gather, 0 = row-major, -1 = by block size
+  int gvm_rows = 1024;     // vector-major general gather: rows per tile
 };
 
 // Kernel launchers (kernels.cu).  `V` is the number of complex values per
@@ -253,8 +255,10 @@ int launch_reorth_pass(const void* Vs, void* w, long long dim, int R, int j, int
 // FP64 [R][M][M]; Gp holds sym_partial_doubles(R, M, nranges) doubles.
 int sym_ranges(long long dim, int R, int M);
 size_t sym_partial_doubles(int R, int M, int nranges);
-int launch_sym_omat(const InstDesc* h, const void* Vs, int R, int M, int nranges, double* Gp, double* G, int c64,
-                    void* stream);
+// W: nullptr, or space for (u.S) q_k of every stored vector (the size of Vs):
+// then formed first and loaded by the contraction.
+int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, int nranges, double* Gp, double* G,
+                    int c64, void* stream);
 
 // Stored-matrix comparison path (csr.cu): count, scan, fill, multiply.
 size_t csr_smem_bytes(const LaunchArgs& a, int c64);

@@ -86,10 +86,36 @@ __device__ __forceinline__ void s_row(const SmemView& s, const TabLayout& L, int
 template <int V>
 __device__ void flush_partials(const LaunchArgs& a, const SmemView& s, int inst, double* acc) {
   const int np = V * kNumPartials;
+  const int C = a.C;
+  if (C <= 32 && (32 % C) == 0) {
+    // the threads of one chunk (tid % C) within a warp are lanes chunk, chunk + C, ...:
+    // add them by shuffles, then the warps' sums in warp order (fixed, deterministic)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < np; ++k) {
+      double v = acc[k];
+      for (int o = 16; o >= C; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[k] = v;
+    }
+    __syncthreads();
+    if (lane < C)
+      for (int k = 0; k < np; ++k) s.red[(warp * C + lane) * np + k] = acc[k];
+    __syncthreads();
+    if ((int)threadIdx.x < C) {
+      double* out = a.partials + ((size_t)inst * gridDim.x + blockIdx.x) * (size_t)a.R * kNumPartials;
+      for (int k = 0; k < np; ++k) {
+        double sum = 0.0;
+        for (int w = 0; w < nw; ++w) sum += s.red[(w * C + threadIdx.x) * np + k];
+        const int v = k / kNumPartials, c = k % kNumPartials;
+        out[(threadIdx.x * V + v) * kNumPartials + c] = sum;
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < np; ++k) acc[k] = 0.0;
+    return;
+  }
   __syncthreads();
   for (int k = 0; k < np; ++k) s.red[threadIdx.x * np + k] = acc[k];
   __syncthreads();
-  const int C = a.C;
   const int per = blockDim.x / C;
   if ((int)threadIdx.x < C) {
     double sum[V * kNumPartials];
@@ -178,8 +204,15 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 1) rows_kernel(co
       const long long e_end = min(row0 + a.rows_per_tile, d.dim) * a.R;
       const long long step = (long long)blockDim.x * V;
       long long e = row0 * a.R + (long long)threadIdx.x * V;
+      // loads of several groups in flight per thread before their stores (the
+      // compiler cannot move a group's loads above the previous group's stores)
+      constexpr int kU = V >= 4 ? 1 : 4 / V;
       if (MODE == kModeStep) {
         step_stream<real, V, 4>(d, a, e, e_end, step, sig, bsp, coef, pacc);
+      } else if (MODE == kModeUpdate) {
+        update_stream<real, V, kU>(d, e, e_end, step, coef, pacc);
+      } else if (MODE == kModeEpilogue) {
+        epilogue_stream<real, V, kU>(d, a, e, e_end, step, sig, bsp, pacc);
       } else {
         for (; e + step < e_end; e += 2 * step) {
           elementwise_item<real, V, MODE>(d, a, e, sig, bsp, coef, pacc);

@@ -7,7 +7,10 @@
 // conj(a) S^-, a = (u_x - i u_y)/2, is one-body, so (u.S) q_j at a row needs
 // q_j at the row itself and at its single-site neighbours mu -+ stride_k.
 //
-// One kernel does both halves: a CTA owns one vector r, a 64 x 64 block of
+// When memory allows, W_k = (u.S) q_k is formed first for every stored vector,
+// vector after vector so that each vector's neighbourhood stays in L2, and
+// the contraction loads it like q.  Otherwise one kernel does both halves: a
+// CTA owns one vector r, a 64 x 64 block of
 // (i, j) and a range of rows.  Per tile of 64 rows (32 in complex128) it stages q_i (the i block)
 // and (u.S) q_j (the j block, formed from the neighbours on the fly) in
 // shared memory, and every thread accumulates 4 x 4 entries of G (rows
@@ -58,9 +61,12 @@ struct SymLayout {
 
 // grid: x = row range, y = (i block, j block), z = vector r.  Gp partials
 // [r][range][M][M] complex FP64 (this CTA's block only).
+// Wv: nullptr, or (u.S) q_k already formed, in the layout of Vs; the B tile
+// is then loaded like the A tile instead of gathered from neighbours.
 template <typename real>
-__global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d, const real* __restrict__ Vs, int R,
-                                                             int M, long long rows_per_range, int nbj,
+__global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d, const real* __restrict__ Vs,
+                                                             const real* __restrict__ Wv, int R, int M,
+                                                             long long rows_per_range, int nbj,
                                                              double* __restrict__ Gp) {
   using v2 = typename Cx<real>::v2;
   using Lay = SymLayout<real>;
@@ -151,13 +157,17 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
       A[ii * kPitch + tt] = v;
     }
     __syncthreads();
-    // (u.S) q_j of the j block from the single-site neighbours
+    // (u.S) q_j of the j block: loaded when formed beforehand, else from the
+    // single-site neighbours
+    const v2* wbase = Wv ? reinterpret_cast<const v2*>(Wv) + (size_t)r * (size_t)dim : nullptr;
     for (int e = threadIdx.x; e < kSymBlock * kRows; e += blockDim.x) {
       const int jj = e / kRows, tt = e % kRows;
       v2 o;
       o.x = 0;
       o.y = 0;
-      if (jj < nj && tt < nt) {
+      if (wbase && jj < nj && tt < nt) {
+        o = __ldg(wbase + (size_t)(j0 + jj) * vstride + (size_t)(m0 + tt));
+      } else if (jj < nj && tt < nt) {
         const v2* x = base + (size_t)(j0 + jj) * vstride;
         const long long mu = m0 + tt;
         real ar = 0, ai = 0;
@@ -218,6 +228,53 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
     }
 }
 
+// W_k = (u.S) q_k for every stored vector k (Vs order), row tiles of one
+// vector in consecutive CTAs (blockIdx.x fastest) so that a vector's
+// single-site neighbourhood is read from HBM once and then served by L2.
+template <typename real>
+__global__ void __launch_bounds__(256) sym_sdir_kernel(const InstDesc d, const real* __restrict__ Vs,
+                                                     real* __restrict__ Wv, int rows_per_cta) {
+  using v2 = typename Cx<real>::v2;
+  const real* t = reinterpret_cast<const real*>(d.tab);
+  const TabLayout& L = d.lay;
+  const int qm = L.qmax, n = d.n;
+  const real uz = (real)d.obs[0], aur = (real)d.obs[1], aui = (real)d.obs[2];
+  const long long dim = d.dim;
+  const v2* x = reinterpret_cast<const v2*>(Vs) + (size_t)blockIdx.y * (size_t)dim;
+  v2* w = reinterpret_cast<v2*>(Wv) + (size_t)blockIdx.y * (size_t)dim;
+  const long long lo = (long long)blockIdx.x * rows_per_cta;
+  const long long hi = min(dim, lo + rows_per_cta);
+  for (long long mu = lo + threadIdx.x; mu < hi; mu += blockDim.x) {
+    unsigned long long rem = (unsigned long long)mu;
+    real ar = 0, ai = 0, ms = 0;
+    for (int k = 0; k < n; ++k) {
+      const unsigned long long qk = (unsigned long long)__ldg(d.q + k);
+      const unsigned long long nq = rem / qk;
+      const int a = (int)(rem - nq * qk);
+      rem = nq;
+      ms += t[L.off_m + k * qm + a];
+      const long long st = __ldg(d.stride + k);
+      if (a >= 1) {  // a S^+ : from mu - stride
+        const real c = t[L.off_up1 + k * qm + a];
+        const v2 xv = __ldg(x + mu - st);
+        ar += c * (aur * xv.x - aui * xv.y);
+        ai += c * (aur * xv.y + aui * xv.x);
+      }
+      if (a + 1 < (int)qk) {  // conj(a) S^- : from mu + stride
+        const real c = t[L.off_dn1 + k * qm + a];
+        const v2 xv = __ldg(x + mu + st);
+        ar += c * (aur * xv.x + aui * xv.y);
+        ai += c * (aur * xv.y - aui * xv.x);
+      }
+    }
+    const v2 xv = __ldg(x + mu);
+    v2 o;
+    o.x = ar + uz * ms * xv.x;
+    o.y = ai + uz * ms * xv.y;
+    w[mu] = o;
+  }
+}
+
 // G[r][i][j] = sum over the row ranges of the partials, in range order.
 __global__ void sym_reduce_kernel(const double* __restrict__ Gp, int R, int M, int nranges, double* __restrict__ G) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,8 +305,8 @@ int sym_ranges(long long dim, int R, int M) {
   return (int)std::min<long long>(ranges, 1 << 20);
 }
 
-int launch_sym_omat(const InstDesc* h, const void* Vs, int R, int M, int nranges, double* Gp, double* G, int c64,
-                    void* stream) {
+int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, int nranges, double* Gp, double* G,
+                    int c64, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (R < 1 || R > 65535 || M < 1 || nranges < 1 || h->n > kMaxSites) return (int)cudaErrorInvalidValue;
   const int nb = (M + kSymBlock - 1) / kSymBlock;
@@ -258,16 +315,26 @@ int launch_sym_omat(const InstDesc* h, const void* Vs, int R, int M, int nranges
   const dim3 grid((unsigned)nranges, (unsigned)(nb * nb), (unsigned)R);
   const int qm = h->lay.qmax;
   cudaError_t e;
+  if (W) {  // (u.S) q_k of every stored vector first, vector by vector
+    const int rows = 1024;
+    const dim3 g1((unsigned)((h->dim + rows - 1) / rows), (unsigned)(R * M));
+    if ((long long)R * M > 65535) return (int)cudaErrorInvalidValue;
+    if (c64) sym_sdir_kernel<float><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, rows);
+    else sym_sdir_kernel<double><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, rows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+  }
   if (c64) {
     const size_t smem = SymLayout<float>::bytes(h->n, qm);
     e = cudaFuncSetAttribute(sym_omat_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    sym_omat_kernel<float><<<grid, kSymThreads, smem, st>>>(*h, (const float*)Vs, R, M, rows, nb, Gp);
+    sym_omat_kernel<float><<<grid, kSymThreads, smem, st>>>(*h, (const float*)Vs, (const float*)W, R, M, rows, nb, Gp);
   } else {
     const size_t smem = SymLayout<double>::bytes(h->n, qm);
     e = cudaFuncSetAttribute(sym_omat_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    sym_omat_kernel<double><<<grid, kSymThreads, smem, st>>>(*h, (const double*)Vs, R, M, rows, nb, Gp);
+    sym_omat_kernel<double><<<grid, kSymThreads, smem, st>>>(*h, (const double*)Vs, (const double*)W, R, M, rows, nb,
+                                                             Gp);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;

@@ -254,3 +254,22 @@ def test_run_rejects_bad_params():
         F.run(s, R=2, M=5, T=[1.0, -1.0])
     with pytest.raises(F.FtlmError):
         F.run(s, R=2, M=5, T=T, start="basis", basis_offset=15)
+
+
+@pytest.mark.parametrize("R", [1, 2, 4, 8, 16])
+def test_ftlm_general_vector_major_matches_oracle(R):
+    """The vector-major general plan (any spins): every vector contiguous and
+    H.v by rows_vm_kernel over groups of V = 8, 4, 2 or 1 vectors (the largest
+    that divides R; at most 4 in complex128), against the oracle step by step
+    (complex128) and in the thermodynamics (complex64)."""
+    w = random_system(np.random.default_rng(26070 + R), [2, 1, 3, 2, 1])   # d = 3*2*4*3*2 = 144
+    s = F.System.from_dict(w)
+    o = oracle.ftlm(osys(w), R=R, M=30, T=T, seed=8, vec_offset=1)
+    g = F.run(s, R=R, M=30, T=T, seed=8, vec_offset=1, dtype="c128")
+    assert g["shape"]["vector_major"] == 1 and g["shape"]["cube_bits"] == 0
+    assert g["shape"]["group_vectors"] == max(v for v in (4, 2, 1) if R % v == 0)
+    compare_tridiag(g, o, 1e-10)
+    g64 = F.run(s, R=R, M=30, T=T, seed=8, vec_offset=1, dtype="c64")
+    assert g64["shape"]["group_vectors"] == max(v for v in (8, 4, 2, 1) if R % v == 0)
+    for k in KEYS:
+        assert rel(g64[k], o[k], 1e-3, T >= 0.1) < 1e-4, k

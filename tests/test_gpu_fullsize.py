@@ -126,3 +126,40 @@ def test_ladder_vector_major_run_first_steps():
     assert g64["shape"]["vector_major"] == 1
     assert abs(g64["alpha"][0, 0] - a0) < 1e-5 * scale
     assert abs(g64["beta"][0, 0] - b0) < 1e-5 * scale
+
+
+def test_general_block_beyond_l2_first_steps_and_autotune():
+    """An s = 1 chain of 12 sites (d = 531,441) with R = 32 complex128
+    vectors: its block (272 MB) exceeds L2, so a run takes the row-major
+    general gather by default; alpha_0, beta_0, p_0 of every vector equal the
+    quantities formed from the oracle's start vectors with ftlm_apply_h and
+    ftlm_apply_sdir.  The autotuner (which also times the vector-major
+    general gather) then picks a shape whose run gives the same scalars."""
+    w = max(W.WORKLOADS["chains_s1_x24"]["system"](), key=lambda v: int(np.prod(v["two_s"] + 1)))
+    s = F.System.from_dict(w)
+    d, R = s.dim, 32
+    assert d == 3 ** 12
+    torch = torch_cuda()
+    g = F.run(s, R=R, M=2, T=T, seed=7, dtype="c128")
+    assert g["shape"]["vector_major"] == 0 and g["shape"]["cube_bits"] == 0
+    x = torch.from_numpy(np.ascontiguousarray(oracle.start_vectors(d, R, seed=7))).cuda()
+    hx = torch.empty_like(x)
+    F.apply_h(s, x, hx, R, "c128")
+    ux = torch.empty_like(x)
+    F.apply_sdir(s, x, ux, R, "c128")
+    a0 = torch.sum(x.conj() * hx, dim=0).real
+    b0 = torch.linalg.vector_norm(hx - a0[None, :] * x, dim=0)
+    p0 = torch.sum(x.conj() * ux, dim=0)
+    a0, b0, p0 = a0.cpu().numpy(), b0.cpu().numpy(), p0.cpu().numpy()
+    scale = np.maximum(np.abs(a0), b0)
+    assert np.all(np.abs(g["alpha"][:, 0] - a0) < 1e-10 * scale)
+    assert np.all(np.abs(g["beta"][:, 0] - b0) < 1e-10 * scale)
+    assert np.all(np.abs(g["p"][:, 0] - p0) < 1e-10 * np.maximum(1.0, np.abs(p0)))
+    try:
+        t = F.run(s, R=R, M=2, T=T, seed=7, dtype="c128", autotune=True)
+        assert t["shape"]["cube_bits"] == 0
+        for k in ("alpha", "beta"):
+            assert np.max(np.abs(t[k] - g[k])) < 1e-10 * scale.max(), k
+    finally:
+        F.tune_shape(s, R, "c128", -1)
+        s.close()
