@@ -218,7 +218,8 @@ typedef struct {
   void* stream;          /* cudaStream_t the run is ordered with; NULL = default stream */
   int symmetric;         /* 1 = also the symmetric estimator of M_B (sFTLM, Eqs. E-2-G/H):
                             keeps all M Lanczos vectors on the device (M x R x dim values of
-                            dtype), forms O_ij = <v_i|u.S|v_j> per vector; one system only */
+                            dtype) and as many for u.S of them, forms O_ij = <v_i|u.S|v_j>
+                            per vector; one system only */
   int reorth;            /* 0 = none (the three-term recurrence of Sec. II.C, two predecessor
                             vectors: the hot path).  1 = full re-orthogonalisation, the optional
                             step of Sec. II.C: after w = H v_j - alpha_j v_j - beta_j v_{j-1},
@@ -266,6 +267,8 @@ typedef struct {
   double gap_ms;          /* time_kernels = 1: summed device time between the end of one Lanczos
                              step's last launch and the start of the next step's first launch
                              (the graph's launch gaps; M - 1 of them) */
+  int site_cube;          /* general vector-major H.v: the 2s+1 rows of the top site each thread
+                             holds as a register cube (0: one row a thread) */
 } ftlm_result;
 
 /*
@@ -353,7 +356,12 @@ ftlm_status ftlm_sums_sym(int R, int M, const int* M_eff, const double* alpha, c
  * The default and the autotuner pick these themselves; this call exists for
  * reproducible experiments and tests.
  *  cube_bits      -1: drop the override (back to the default / autotuned
- *                 shape).  0: the general mixed-radix row kernel.  2..4: (every site
+ *                 shape).  0: the general mixed-radix kernel, on the row-major
+ *                 block (multipass 0) or, in ftlm_run and ftlm_run_batch, on
+ *                 the vector-major block (multipass 1; group_vectors = the
+ *                 vectors of one register cube of the top site's 2s+1 rows,
+ *                 4 or 8, or 0 for one row a thread; tile_cubes = rows, or
+ *                 bases of the cube, per tile in units of 256).  2..4: (every site
  *                 s = 1/2 only) the register-cube kernel in which each thread
  *                 owns 2^cube_bits consecutive rows of one vector.
  *  group_vectors  register-cube kernel: vectors processed together (the

@@ -62,7 +62,7 @@ class Result(ctypes.Structure):
         ("grid", ctypes.c_int), ("threads", ctypes.c_int), ("vector_major", ctypes.c_int),
         ("M_B_sym", ctypes.POINTER(ctypes.c_double)), ("M_B_sym_imag", ctypes.POINTER(ctypes.c_double)),
         ("O_lanczos", ctypes.POINTER(ctypes.c_double)), ("sym_ms", ctypes.c_double),
-        ("gap_ms", ctypes.c_double),
+        ("gap_ms", ctypes.c_double), ("site_cube", ctypes.c_int),
     ]
 
 
@@ -342,7 +342,8 @@ def _finish(r, out):
                kernel_launches=r.kernel_launches, h2d_bytes=int(r.h2d_bytes), d2h_bytes=int(r.d2h_bytes),
                shape={"cube_bits": r.cube_bits, "passes": r.passes, "group_vectors": r.group_vectors,
                       "tile_rows": r.tile_rows,
-                      "grid": r.grid, "threads": r.threads, "vector_major": r.vector_major})
+                      "grid": r.grid, "threads": r.threads, "vector_major": r.vector_major,
+                      "site_cube": r.site_cube})
     if "M_B_sym" in out:
         out["sym_ms"] = r.sym_ms
     return out

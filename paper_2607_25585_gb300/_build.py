@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libftlm_gb300.so")
-SOURCES = ["kernels.cu", "hv_half.cu", "hv_vm.cu", "csr.cu", "reorth.cu", "sym.cu", "api.cu", "tables.cpp", "tridiag.cpp"]
+SOURCES = ["kernels.cu", "hv_half.cu", "hv_vm.cu", "hv_cube.cu", "csr.cu", "reorth.cu", "sym.cu", "api.cu", "tables.cpp", "tridiag.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

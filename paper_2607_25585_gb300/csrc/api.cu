@@ -187,6 +187,7 @@ struct Plan {
   // H.v runs rows_vm_kernel over groups of gvm_V vectors of one system
   bool gen_vm = false;
   int gvm_V = 1, gvm_groups = 0, gvm_ntiles = 0, gvm_rows = 0, gvm_grid = 0;
+  int gvm_cube = 0;  // > 0: cube_gather_kernel with the top site's 2s+1 rows per thread
   size_t gvm_smem = 0;
   std::vector<int> tile_start_g;  // prefix sum of H.v tiles over the groups
 };
@@ -365,12 +366,20 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
     }
   }
   // runs on other systems and batches: the vector-major general gather by
-  // default when the largest system's block of R vectors fits in L2 (measured
-  // on GB300: 24 % faster than the row-major gather on s = 1 chains whose
-  // largest block is 68 MB, 5 % slower on a 150 MB mixed-spin block), else
-  // the row-major one; an autotuned or forced shape decides for itself
+  // default when it can hold the top site's rows as a register cube (every
+  // system with the same top spin, a group size dividing R), or when the
+  // largest system's block of R vectors fits in L2; else the row-major one.
+  // Measured on GB300: with one row a thread the vector-major gather is 24 %
+  // faster than the row-major one on s = 1 chains whose largest block is
+  // 68 MB but 5 % slower on a 150 MB mixed-spin block, where the cube form is
+  // 17 % faster than both.  An autotuned or forced shape decides for itself.
+  int Qtop = sys[0]->hs.n >= 2 ? sys[0]->hs.q.back() : 0;
+  for (auto* s : sys)
+    if (s->hs.n < 2 || s->hs.q.back() != Qtop) Qtop = 0;
+  const int Vdef = Qtop ? cube_vectors(Qtop, c64) : 0;
   const bool gvm_fits = (long long)big->hs.dim * R * (c64 ? 8 : 16) <= device_l2_bytes();
-  const bool want_gvm = pl.sh.general_vm == 1 || (pl.sh.general_vm < 0 && !force && gvm_fits);
+  const bool gvm_default = gvm_fits || (Vdef > 0 && R % Vdef == 0);
+  const bool want_gvm = pl.sh.general_vm == 1 || (pl.sh.general_vm < 0 && !force && gvm_default);
   if (allow_vm && want_gvm && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
     int V = 1;
     for (int v : {8, 4, 2, 1})
@@ -378,6 +387,12 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
         V = v;
         break;
       }
+    // the register cube along the top site when every system has the same top
+    // spin and a kernel exists for it and for a group size dividing R
+    const int Q = Qtop;
+    const int Vc = (Q && pl.sh.gvm_cube != 0) ? cube_vectors(Q, c64, std::max(0, pl.sh.gvm_cube)) : 0;
+    const bool cube = Vc > 0 && R % Vc == 0;
+    if (cube) V = Vc;
     std::vector<ftlm_system*> vecs;  // one instance per (system, vector), system-major
     for (auto* s : sys)
       for (int k = 0; k < R; ++k) vecs.push_back(s);
@@ -388,19 +403,29 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
     pl.sh.half_K = keep.half_K;
     pl.gen_vm = true;
     pl.gvm_V = V;
-    pl.gvm_rows = keep.gvm_rows > 0 ? keep.gvm_rows : 1024;  // 1024: four rows a thread of a 256-thread CTA
+    pl.gvm_cube = cube ? Q : 0;
+    // 1024 rows: four a thread of a 256-thread CTA; with the cube, 256 bases
+    // (one a thread: the CTAs then share the neighbourhoods they gather in L2)
+    pl.gvm_rows = keep.gvm_rows > 0 && keep.general_vm == 1 ? keep.gvm_rows : (cube ? 256 : 1024);
     pl.tile_start_g.assign(1, 0);
     for (auto* s : sys)
       for (int g = 0; g < R / V; ++g) {
-        const long long tiles = ((long long)s->hs.dim + pl.gvm_rows - 1) / pl.gvm_rows;
+        const long long rows = cube ? (long long)s->hs.dim / Q : (long long)s->hs.dim;  // bases, or rows
+        const long long tiles = (rows + pl.gvm_rows - 1) / pl.gvm_rows;
         if (pl.tile_start_g.back() + tiles > (1ll << 30)) return fail(FTLM_ERR_UNSUPPORTED, "too many tiles");
         pl.tile_start_g.push_back(pl.tile_start_g.back() + (int)tiles);
       }
     pl.gvm_groups = (int)pl.tile_start_g.size() - 1;
     pl.gvm_ntiles = pl.tile_start_g.back();
     pl.gvm_smem = pl.smem;  // the same tables and per-thread columns as the streaming plan
-    CKI(prepare_rows_vm(V, c64, std::max<size_t>(pl.gvm_smem, 48 * 1024)));
-    const int per_sm = rows_vm_ctas_per_sm(V, c64, 256, pl.gvm_smem);
+    int per_sm = 1;
+    if (cube) {
+      CKI(prepare_cube(Q, V, c64, std::max<size_t>(pl.gvm_smem, 48 * 1024)));
+      per_sm = cube_ctas_per_sm(Q, V, c64, 256, pl.gvm_smem);
+    } else {
+      CKI(prepare_rows_vm(V, c64, std::max<size_t>(pl.gvm_smem, 48 * 1024)));
+      per_sm = rows_vm_ctas_per_sm(V, c64, 256, pl.gvm_smem);
+    }
     pl.gvm_grid = std::max(1, std::min(pl.gvm_ntiles, std::max(1, device_sm_count()) * per_sm));
     return FTLM_OK;
   }
@@ -422,6 +447,7 @@ int launch_plan(const Plan& pl, LaunchArgs a, void* st) {
     a.ntiles = pl.gvm_ntiles;
     a.rows_per_tile = pl.gvm_rows;
     if (!a.inline_one) a.tile_start += pl.base.n_inst + 1;
+    if (pl.gvm_cube) return launch_cube(a, pl.gvm_cube, pl.gvm_V, pl.c64, pl.gvm_grid, 256, pl.gvm_smem, st);
     return launch_rows_vm(a, pl.gvm_V, pl.c64, pl.gvm_grid, 256, pl.gvm_smem, st);
   }
   if (pl.half.on && pl.half.vm && (a.mode == kModeStep || a.mode == kModeStartNorm || a.mode == kModeUpdate)) {
@@ -651,7 +677,9 @@ std::string run_key(const std::vector<ftlm_system*>& sys, const ftlm_run_params*
   k += buf;
   k += p->symmetric ? "|sym" : "";
   k += p->reorth ? "|reorth" : "";
-  k += pl.gen_vm ? "|gvm" + std::to_string(pl.gvm_V) + "x" + std::to_string(pl.gvm_rows) : "";
+  k += pl.gen_vm ? "|gvm" + std::to_string(pl.gvm_V) + "x" + std::to_string(pl.gvm_rows) + "c" +
+                       std::to_string(pl.gvm_cube)
+                 : "";
   snprintf(buf, sizeof buf, "|half%d vm%d hy%d K%d Rg%d rpt%d g%d P%d mb%d", pl.half.on ? 1 : 0, pl.half.vm ? 1 : 0,
            pl.half.hybrid ? 1 : 0,
            pl.half.K, pl.half.Rg, pl.half.rows_per_tile, pl.half.grid, pl.half.passes, pl.half.min_blocks);
@@ -939,14 +967,14 @@ ftlm_status symmetric_matrices(ftlm_system* s, const ftlm_run_params* p, cudaStr
     s->Od.release();
     if (s->Od.ensure(obytes) != cudaSuccess) return fail(FTLM_ERR_OUT_OF_MEMORY, "O matrices");
   }
-  // u.S q_k of all stored vectors beforehand when their copy fits (the size of
-  // the stored vectors); else the contraction forms them tile by tile
+  // u.S q_k of all stored vectors (as large as the stored vectors)
   const size_t wbytes = (size_t)d * R * (c64 ? 8 : 16) * M;
   if (s->Ws.bytes < wbytes) {
     s->Ws.release();
-    if (s->Ws.ensure(wbytes) != cudaSuccess) cudaGetLastError();  // (a failed allocation leaves Ws empty)
+    if (s->Ws.ensure(wbytes) != cudaSuccess)
+      return fail(FTLM_ERR_OUT_OF_MEMORY, "symmetric run: " + std::to_string(wbytes) + " bytes for u.S of the Lanczos vectors");
   }
-  void* W = s->Ws.bytes >= wbytes ? s->Ws.p : nullptr;
+  void* W = s->Ws.p;
   InstDesc hd = base_desc(s, c64);
   observable_coefs(s->hs, p->obs_dir, hd.obs);
   cudaEvent_t e0, e1;
@@ -1119,6 +1147,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
     out.grid = pl.half.on ? pl.half.grid : (pl.gen_vm ? pl.gvm_grid : pl.grid);
     out.threads = pl.half.on ? pl.half.threads : (pl.gen_vm ? 256 : pl.sh.threads);
     out.vector_major = plan_vmaj(pl) ? 1 : 0;
+    out.site_cube = pl.gen_vm ? pl.gvm_cube : 0;
     out.sym_ms = 0.0;
     if (p->symmetric) {  // Eqs. (E-2-G), (E-2-H)
       const double* sigma_d = p_d + (size_t)M * R * 2;  // [M][R]
@@ -1189,12 +1218,14 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
         sh.general_vm = 0;
         cands.push_back(sh);
       }
-    for (int rows : {512, 1024, 2048}) {  // the vector-major general gather (runs only)
-      Shape sh = default_shape(R, c64);
-      sh.general_vm = 1;
-      sh.gvm_rows = rows;
-      cands.push_back(sh);
-    }
+    for (int cube : {8, 4, 0})  // the vector-major general gather (runs only): cube over 8 or 4 vectors, none
+      for (int rows : {256, 512, 1024, 2048}) {
+        Shape sh = default_shape(R, c64);
+        sh.general_vm = 1;
+        sh.gvm_rows = rows;
+        sh.gvm_cube = cube;
+        cands.push_back(sh);
+      }
   }
   ftlm_status w = ensure_workspace(s, R, 1, c64);
   if (w != FTLM_OK) return w;
@@ -1224,7 +1255,7 @@ ftlm_status autotune(ftlm_system* s, int R, int c64, cudaStream_t st) {
     Plan pl;
     if (make_plan(one, R, c64, pl, &sh, sh.half_vm != 0 || sh.general_vm == 1) != FTLM_OK) continue;
     if (sh.half_K > 0 && (!pl.half.on || pl.half.vm != (sh.half_vm != 0))) continue;
-    if (sh.general_vm == 1 && !pl.gen_vm) continue;
+    if (sh.general_vm == 1 && (!pl.gen_vm || (sh.gvm_cube > 0 && (!pl.gvm_cube || pl.gvm_V != sh.gvm_cube)))) continue;
     LaunchArgs a = pl.base;
     if (pl.half.vm) {
       a.inst = reinterpret_cast<const InstDesc*>(vdesc.p);
@@ -1654,7 +1685,16 @@ ftlm_status ftlm_tune_shape(const ftlm_system* s, int nvec, ftlm_dtype dtype, in
     return FTLM_OK;
   }
   Shape sh = default_shape(nvec, c64);
-  sh.explicit_general = cube_bits == 0;
+  sh.explicit_general = cube_bits == 0 && multipass == 0;
+  if (cube_bits == 0 && multipass != 0) {  // the vector-major general gather
+    if (multipass != 1) return fail(FTLM_ERR_INVALID_ARG, "multipass must be 0 or 1 with cube_bits 0");
+    if (group_vectors < 0 || group_vectors > 8 || nvec % std::max(1, group_vectors) != 0)
+      return fail(FTLM_ERR_INVALID_ARG, "group_vectors must be 0 or a group size (4, 8) dividing nvec");
+    if (tile_cubes < 1 || tile_cubes > 64) return fail(FTLM_ERR_INVALID_ARG, "tile_cubes must be in 1..64");
+    sh.general_vm = 1;
+    sh.gvm_cube = group_vectors;
+    sh.gvm_rows = 256 * tile_cubes;
+  }
   if (cube_bits != 0) {
     if (!s->hs.all_half) return fail(FTLM_ERR_UNSUPPORTED, "register cubes need every site s = 1/2");
     if (cube_bits < 2 || cube_bits > 4 || s->hs.n < cube_bits + 2)

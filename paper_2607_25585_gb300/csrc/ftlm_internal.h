@@ -188,6 +188,9 @@ struct Shape {
   bool explicit_general = false;  // set by the caller: general kernel even for spin-1/2
   int general_vm = -1;     // general kernel in runs: 1 = vector-major gather, 0 = row-major, -1 = by block size
   int gvm_rows = 1024;     // vector-major general gather: rows per tile
+  int gvm_cube = -1;       // vector-major general gather: > 0 = register cube of the top site over groups
+                           // of that many vectors, 0 = one row a thread, -1 = the cube with the default
+                           // group size where a kernel exists for the top site's 2s+1 and R
 };
 
 // Kernel launchers (kernels.cu).  `V` is the number of complex values per
@@ -216,6 +219,14 @@ int rows_vm_supported(int V, int c64);
 int prepare_rows_vm(int V, int c64, size_t smem);
 int rows_vm_ctas_per_sm(int V, int c64, int threads, size_t smem);
 int launch_rows_vm(const LaunchArgs& a, int V, int c64, int grid, int threads, size_t smem, void* stream);
+// The vector-major general H.v with a register cube of the top site's Q = 2s+1
+// rows (hv_cube.cu), over groups of cube_vectors(Q, c64) vectors (0: no
+// kernel for this Q; want > 0 asks for that group size); tiles are ranges of
+// bases (rows with top digit 0).
+int cube_vectors(int Q, int c64, int want = 0);
+int prepare_cube(int Q, int V, int c64, size_t smem);
+int cube_ctas_per_sm(int Q, int V, int c64, int threads, size_t smem);
+int launch_cube(const LaunchArgs& a, int Q, int V, int c64, int grid, int threads, size_t smem, void* stream);
 int device_sm_count();
 long long device_l2_bytes();
 
@@ -255,8 +266,8 @@ int launch_reorth_pass(const void* Vs, void* w, long long dim, int R, int j, int
 // FP64 [R][M][M]; Gp holds sym_partial_doubles(R, M, nranges) doubles.
 int sym_ranges(long long dim, int R, int M);
 size_t sym_partial_doubles(int R, int M, int nranges);
-// W: nullptr, or space for (u.S) q_k of every stored vector (the size of Vs):
-// then formed first and loaded by the contraction.
+// W: space for (u.S) q_k of every stored vector (the size of Vs), formed
+// first and then loaded by the contraction.
 int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, int nranges, double* Gp, double* G,
                     int c64, void* stream);
 

@@ -7,15 +7,13 @@
 // conj(a) S^-, a = (u_x - i u_y)/2, is one-body, so (u.S) q_j at a row needs
 // q_j at the row itself and at its single-site neighbours mu -+ stride_k.
 //
-// When memory allows, W_k = (u.S) q_k is formed first for every stored vector,
-// vector after vector so that each vector's neighbourhood stays in L2, and
-// the contraction loads it like q.  Otherwise one kernel does both halves: a
-// CTA owns one vector r, a 64 x 64 block of
-// (i, j) and a range of rows.  Per tile of 64 rows (32 in complex128) it stages q_i (the i block)
-// and (u.S) q_j (the j block, formed from the neighbours on the fly) in
-// shared memory, and every thread accumulates 4 x 4 entries of G (rows
-// ti + 16a, columns tj + 16b of the block) in registers.  (u.S) q_j is never
-// written to device memory.  The CTA writes its partial block; a second
+// W_k = (u.S) q_k is formed first for every stored vector, vector after
+// vector so that each vector's single-site neighbourhood stays in L2; then a
+// contraction kernel in which a CTA owns one vector r, a 64 x 64 block of
+// (i, j) and a range of rows.  Per tile of 64 rows (32 in complex128) it
+// stages q_i (the i block) and W_j (the j block) in shared memory, and every
+// thread accumulates 4 x 4 entries of G (rows ti + 16a, columns tj + 16b of
+// the block) in registers.  The CTA writes its partial block; a second
 // kernel adds the partials of all row ranges in a fixed order in FP64
 // (deterministic for a given launch shape).
 //
@@ -41,74 +39,40 @@ struct SymRows {
   static constexpr int value = sizeof(real) == 4 ? 64 : 32;
 };
 
-// Dynamic shared memory: the A and B tiles, the row digits [site][row], the
-// S^z sums of the rows, and the site tables (m, <a|s+|a-1>, <a|s-|a+1>) with
-// the radices and strides.
+// Dynamic shared memory: the A and B tiles.
 template <typename real>
 struct SymLayout {
   static constexpr int kRows = SymRows<real>::value;
   static constexpr int kPitch = kRows + 1;
   static size_t tile_bytes() { return sizeof(typename Cx<real>::v2) * kSymBlock * kPitch; }
-  static size_t bytes(int n, int qm) {
-    size_t b = 2 * tile_bytes();
-    b += (size_t)kRows * sizeof(real);                          // msum
-    b += (((size_t)n * kRows + 15) / 16) * 16;                  // digits
-    b += (((size_t)3 * n * qm * sizeof(real) + 15) / 16) * 16;  // m, up1, dn1
-    b += (size_t)n * 8 + (size_t)n * 4;                         // strides, radices
-    return b;
-  }
 };
 
 // grid: x = row range, y = (i block, j block), z = vector r.  Gp partials
 // [r][range][M][M] complex FP64 (this CTA's block only).
-// Wv: nullptr, or (u.S) q_k already formed, in the layout of Vs; the B tile
-// is then loaded like the A tile instead of gathered from neighbours.
+// The contraction G_r = Q_r^H W_r.  The next tile's loads are issued into registers before the current tile's
+// multiply-adds (all of a thread's loads in flight at once), so their latency
+// is hidden behind the arithmetic instead of paid once per element.
 template <typename real>
-__global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d, const real* __restrict__ Vs,
-                                                             const real* __restrict__ Wv, int R, int M,
-                                                             long long rows_per_range, int nbj,
-                                                             double* __restrict__ Gp) {
+__global__ void __launch_bounds__(kSymThreads, sizeof(real) == 4 ? 2 : 1) sym_omat_kernel(const real* __restrict__ Vs,
+                                                               const real* __restrict__ Wv, long long dim, int R,
+                                                               int M, long long rows_per_range, int nbj,
+                                                               double* __restrict__ Gp) {
   using v2 = typename Cx<real>::v2;
   using Lay = SymLayout<real>;
   constexpr int kRows = Lay::kRows, kPitch = Lay::kPitch;
+  constexpr int kPer = kSymBlock * kRows / kSymThreads;  // tile elements per thread
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = d.n, qm = d.lay.qmax;
-  v2* A = reinterpret_cast<v2*>(smem);                       // [kSymBlock][kPitch]
-  v2* B = A + kSymBlock * kPitch;                            // [kSymBlock][kPitch]
-  real* msum = reinterpret_cast<real*>(B + kSymBlock * kPitch);
-  unsigned char* dig = reinterpret_cast<unsigned char*>(msum + kRows);  // [n][kRows]
-  real* tm = reinterpret_cast<real*>(dig + (((size_t)n * kRows + 15) / 16) * 16);  // [n][qm]
-  real* tup = tm + n * qm;
-  real* tdn = tup + n * qm;
-  long long* sst = reinterpret_cast<long long*>(
-      reinterpret_cast<unsigned char*>(tm) + (((size_t)3 * n * qm * sizeof(real) + 15) / 16) * 16);
-  int* sq = reinterpret_cast<int*>(sst + n);
-
+  v2* A = reinterpret_cast<v2*>(smem);  // [kSymBlock][kPitch]
+  v2* B = A + kSymBlock * kPitch;       // [kSymBlock][kPitch]
   const int r = blockIdx.z;
   const int ib = blockIdx.y / nbj, jb = blockIdx.y % nbj;
   const int i0 = ib * kSymBlock, j0 = jb * kSymBlock;
   const int ni = min(kSymBlock, M - i0), nj = min(kSymBlock, M - j0);
-  const long long dim = d.dim;
   const long long mu_lo = (long long)blockIdx.x * rows_per_range;
   const long long mu_hi = min(dim, mu_lo + rows_per_range);
-  const real uz = (real)d.obs[0], aur = (real)d.obs[1], aui = (real)d.obs[2];
-  const size_t vstride = (size_t)R * (size_t)dim;  // elements between steps k and k + 1
-  const v2* base = reinterpret_cast<const v2*>(Vs) + (size_t)r * (size_t)dim;
-  {
-    const real* t = reinterpret_cast<const real*>(d.tab);
-    for (int e = threadIdx.x; e < n * qm; e += blockDim.x) {
-      tm[e] = t[d.lay.off_m + e];
-      tup[e] = t[d.lay.off_up1 + e];
-      tdn[e] = t[d.lay.off_dn1 + e];
-    }
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      sst[k] = d.stride[k];
-      sq[k] = d.q[k];
-    }
-  }
-  // this thread's entries of the 64 x 64 block: rows ti + 16a, columns tj + 16b
-  // (a half-warp reads 16 consecutive rows of B: no bank conflicts); a thread
-  // skips the rows and columns beyond M (warp-uniform for the rows)
+  const size_t vstride = (size_t)R * (size_t)dim;
+  const v2* abase = reinterpret_cast<const v2*>(Vs) + (size_t)r * (size_t)dim + (size_t)i0 * vstride;
+  const v2* bbase = reinterpret_cast<const v2*>(Wv) + (size_t)r * (size_t)dim + (size_t)j0 * vstride;
   const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
   const int na = (ni - ti + 15) / 16, nbb = (nj - tj + 15) / 16;
   real gr[4][4], gi[4][4];
@@ -116,86 +80,31 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) gr[a][b] = gi[a][b] = 0;
-  const bool idx32 = dim <= 0xffffffffll;
-
+  v2 pa[kPer], pb[kPer];
+  auto load = [&](long long m0) {
+    const int nt = (int)min((long long)kRows, mu_hi - m0);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = threadIdx.x + u * kSymThreads;
+      const int k = e / kRows, tt = e % kRows;
+      pa[u].x = pa[u].y = pb[u].x = pb[u].y = 0;
+      if (k < ni && tt < nt) pa[u] = __ldg(abase + (size_t)k * vstride + (size_t)(m0 + tt));
+      if (k < nj && tt < nt) pb[u] = __ldg(bbase + (size_t)k * vstride + (size_t)(m0 + tt));
+    }
+  };
+  if (mu_lo < mu_hi) load(mu_lo);
   for (long long m0 = mu_lo; m0 < mu_hi; m0 += kRows) {
     const int nt = (int)min((long long)kRows, mu_hi - m0);
-    __syncthreads();
-    // digits and the S^z sum of the tile's rows
-    for (int tt = threadIdx.x; tt < nt; tt += blockDim.x) {
-      real ms = 0;
-      if (idx32) {
-        unsigned rem = (unsigned)(m0 + tt);
-        for (int k = 0; k < n; ++k) {
-          const unsigned qk = (unsigned)sq[k];
-          const unsigned nq = rem / qk;
-          const int a = (int)(rem - nq * qk);
-          rem = nq;
-          dig[k * kRows + tt] = (unsigned char)a;
-          ms += tm[k * qm + a];
-        }
-      } else {
-        unsigned long long rem = (unsigned long long)(m0 + tt);
-        for (int k = 0; k < n; ++k) {
-          const unsigned long long qk = (unsigned long long)sq[k];
-          const unsigned long long nq = rem / qk;
-          const int a = (int)(rem - nq * qk);
-          rem = nq;
-          dig[k * kRows + tt] = (unsigned char)a;
-          ms += tm[k * qm + a];
-        }
-      }
-      msum[tt] = ms;
-    }
-    // q_i of the i block
-    for (int e = threadIdx.x; e < kSymBlock * kRows; e += blockDim.x) {
-      const int ii = e / kRows, tt = e % kRows;
-      v2 v;
-      v.x = 0;
-      v.y = 0;
-      if (ii < ni && tt < nt) v = __ldg(base + (size_t)(i0 + ii) * vstride + (size_t)(m0 + tt));
-      A[ii * kPitch + tt] = v;
+    __syncthreads();  // the previous tile's multiply-adds are done
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = threadIdx.x + u * kSymThreads;
+      const int k = e / kRows, tt = e % kRows;
+      A[k * kPitch + tt] = pa[u];
+      B[k * kPitch + tt] = pb[u];
     }
     __syncthreads();
-    // (u.S) q_j of the j block: loaded when formed beforehand, else from the
-    // single-site neighbours
-    const v2* wbase = Wv ? reinterpret_cast<const v2*>(Wv) + (size_t)r * (size_t)dim : nullptr;
-    for (int e = threadIdx.x; e < kSymBlock * kRows; e += blockDim.x) {
-      const int jj = e / kRows, tt = e % kRows;
-      v2 o;
-      o.x = 0;
-      o.y = 0;
-      if (wbase && jj < nj && tt < nt) {
-        o = __ldg(wbase + (size_t)(j0 + jj) * vstride + (size_t)(m0 + tt));
-      } else if (jj < nj && tt < nt) {
-        const v2* x = base + (size_t)(j0 + jj) * vstride;
-        const long long mu = m0 + tt;
-        real ar = 0, ai = 0;
-        for (int k = 0; k < n; ++k) {
-          const int a = dig[k * kRows + tt];
-          const long long st = sst[k];
-          if (a >= 1) {  // a S^+ : from mu - stride
-            const real c = tup[k * qm + a];
-            const v2 xv = __ldg(x + mu - st);
-            ar += c * (aur * xv.x - aui * xv.y);
-            ai += c * (aur * xv.y + aui * xv.x);
-          }
-          if (a + 1 < sq[k]) {  // conj(a) S^- : from mu + stride
-            const real c = tdn[k * qm + a];
-            const v2 xv = __ldg(x + mu + st);
-            ar += c * (aur * xv.x + aui * xv.y);
-            ai += c * (aur * xv.y - aui * xv.x);
-          }
-        }
-        const v2 xv = __ldg(x + mu);
-        const real dz = uz * msum[tt];
-        o.x = ar + dz * xv.x;
-        o.y = ai + dz * xv.y;
-      }
-      B[jj * kPitch + tt] = o;
-    }
-    __syncthreads();
-    // G[i][j] += conj(A[i][mu]) B[j][mu]
+    if (m0 + kRows < mu_hi) load(m0 + kRows);
     for (int tt = 0; tt < nt; ++tt) {
       v2 av[4], bv[4];
 #pragma unroll
@@ -214,7 +123,6 @@ __global__ void __launch_bounds__(kSymThreads) sym_omat_kernel(const InstDesc d,
       }
     }
   }
-  // this CTA's partial block
   double* out = Gp + ((size_t)r * gridDim.x + blockIdx.x) * (size_t)M * M * 2;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -244,14 +152,23 @@ __global__ void __launch_bounds__(256) sym_sdir_kernel(const InstDesc d, const r
   v2* w = reinterpret_cast<v2*>(Wv) + (size_t)blockIdx.y * (size_t)dim;
   const long long lo = (long long)blockIdx.x * rows_per_cta;
   const long long hi = min(dim, lo + rows_per_cta);
+  const bool idx32 = dim <= 0xffffffffll;  // 32-bit digit division when the rows allow it
   for (long long mu = lo + threadIdx.x; mu < hi; mu += blockDim.x) {
     unsigned long long rem = (unsigned long long)mu;
+    unsigned rem32 = (unsigned)mu;
     real ar = 0, ai = 0, ms = 0;
     for (int k = 0; k < n; ++k) {
-      const unsigned long long qk = (unsigned long long)__ldg(d.q + k);
-      const unsigned long long nq = rem / qk;
-      const int a = (int)(rem - nq * qk);
-      rem = nq;
+      const int qk = __ldg(d.q + k);
+      int a;
+      if (idx32) {
+        const unsigned nq = rem32 / (unsigned)qk;
+        a = (int)(rem32 - nq * (unsigned)qk);
+        rem32 = nq;
+      } else {
+        const unsigned long long nq = rem / (unsigned long long)qk;
+        a = (int)(rem - nq * (unsigned long long)qk);
+        rem = nq;
+      }
       ms += t[L.off_m + k * qm + a];
       const long long st = __ldg(d.stride + k);
       if (a >= 1) {  // a S^+ : from mu - stride
@@ -260,7 +177,7 @@ __global__ void __launch_bounds__(256) sym_sdir_kernel(const InstDesc d, const r
         ar += c * (aur * xv.x - aui * xv.y);
         ai += c * (aur * xv.y + aui * xv.x);
       }
-      if (a + 1 < (int)qk) {  // conj(a) S^- : from mu + stride
+      if (a + 1 < qk) {  // conj(a) S^- : from mu + stride
         const real c = t[L.off_dn1 + k * qm + a];
         const v2 xv = __ldg(x + mu + st);
         ar += c * (aur * xv.x + aui * xv.y);
@@ -308,33 +225,33 @@ int sym_ranges(long long dim, int R, int M) {
 int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, int nranges, double* Gp, double* G,
                     int c64, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (R < 1 || R > 65535 || M < 1 || nranges < 1 || h->n > kMaxSites) return (int)cudaErrorInvalidValue;
+  if (!W || R < 1 || R > 65535 || M < 1 || nranges < 1 || h->n > kMaxSites) return (int)cudaErrorInvalidValue;
   const int nb = (M + kSymBlock - 1) / kSymBlock;
-  if ((long long)nb * nb > 65535) return (int)cudaErrorInvalidValue;
-  const long long rows = (h->dim + nranges - 1) / nranges;
+  if ((long long)nb * nb > 65535 || (long long)R * M > 65535) return (int)cudaErrorInvalidValue;
+  const long long dim = h->dim;
+  const long long rows = (dim + nranges - 1) / nranges;
   const dim3 grid((unsigned)nranges, (unsigned)(nb * nb), (unsigned)R);
-  const int qm = h->lay.qmax;
   cudaError_t e;
-  if (W) {  // (u.S) q_k of every stored vector first, vector by vector
-    const int rows = 1024;
-    const dim3 g1((unsigned)((h->dim + rows - 1) / rows), (unsigned)(R * M));
-    if ((long long)R * M > 65535) return (int)cudaErrorInvalidValue;
-    if (c64) sym_sdir_kernel<float><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, rows);
-    else sym_sdir_kernel<double><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, rows);
+  {  // (u.S) q_k of every stored vector, vector by vector
+    const int trows = 1024;
+    const dim3 g1((unsigned)((dim + trows - 1) / trows), (unsigned)(R * M));
+    if (c64) sym_sdir_kernel<float><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, trows);
+    else sym_sdir_kernel<double><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, trows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
   }
   if (c64) {
-    const size_t smem = SymLayout<float>::bytes(h->n, qm);
+    const size_t smem = 2 * SymLayout<float>::tile_bytes();
     e = cudaFuncSetAttribute(sym_omat_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    sym_omat_kernel<float><<<grid, kSymThreads, smem, st>>>(*h, (const float*)Vs, (const float*)W, R, M, rows, nb, Gp);
+    sym_omat_kernel<float><<<grid, kSymThreads, smem, st>>>((const float*)Vs, (const float*)W, dim, R, M, rows, nb,
+                                                              Gp);
   } else {
-    const size_t smem = SymLayout<double>::bytes(h->n, qm);
+    const size_t smem = 2 * SymLayout<double>::tile_bytes();
     e = cudaFuncSetAttribute(sym_omat_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    sym_omat_kernel<double><<<grid, kSymThreads, smem, st>>>(*h, (const double*)Vs, (const double*)W, R, M, rows, nb,
-                                                             Gp);
+    sym_omat_kernel<double><<<grid, kSymThreads, smem, st>>>((const double*)Vs, (const double*)W, dim, R, M, rows,
+                                                               nb, Gp);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;

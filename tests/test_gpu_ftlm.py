@@ -259,9 +259,10 @@ def test_run_rejects_bad_params():
 @pytest.mark.parametrize("R", [1, 2, 4, 8, 16])
 def test_ftlm_general_vector_major_matches_oracle(R):
     """The vector-major general plan (any spins): every vector contiguous and
-    H.v by rows_vm_kernel over groups of V = 8, 4, 2 or 1 vectors (the largest
-    that divides R; at most 4 in complex128), against the oracle step by step
-    (complex128) and in the thermodynamics (complex64)."""
+    H.v over groups of V vectors -- the register cube of the top site where
+    its group size divides R, else rows_vm_kernel with the largest of 8, 4, 2,
+    1 (at most 4 in complex128) that divides R -- against the oracle step by
+    step (complex128) and in the thermodynamics (complex64)."""
     w = random_system(np.random.default_rng(26070 + R), [2, 1, 3, 2, 1])   # d = 3*2*4*3*2 = 144
     s = F.System.from_dict(w)
     o = oracle.ftlm(osys(w), R=R, M=30, T=T, seed=8, vec_offset=1)
@@ -269,7 +270,82 @@ def test_ftlm_general_vector_major_matches_oracle(R):
     assert g["shape"]["vector_major"] == 1 and g["shape"]["cube_bits"] == 0
     assert g["shape"]["group_vectors"] == max(v for v in (4, 2, 1) if R % v == 0)
     compare_tridiag(g, o, 1e-10)
+    # the top site is s = 1/2: a register cube of its 2 rows where the group size divides R
+    assert g["shape"]["site_cube"] == (2 if R % 4 == 0 else 0)
     g64 = F.run(s, R=R, M=30, T=T, seed=8, vec_offset=1, dtype="c64")
-    assert g64["shape"]["group_vectors"] == max(v for v in (8, 4, 2, 1) if R % v == 0)
+    if R % 8 == 0:  # the cube over groups of 8 vectors (complex64, 2s+1 <= 3)
+        assert g64["shape"]["site_cube"] == 2 and g64["shape"]["group_vectors"] == 8
+    else:
+        assert g64["shape"]["site_cube"] == 0 and g64["shape"]["group_vectors"] == R
     for k in KEYS:
         assert rel(g64[k], o[k], 1e-3, T >= 0.1) < 1e-4, k
+
+
+@pytest.mark.parametrize("top", [2, 3, 4, 5])
+def test_ftlm_site_cube_matches_oracle(top):
+    """The general gather with a register cube of the top site's 2s+1 rows
+    (s = 1 .. 5/2, every single-site, double-flip and pair term of the top
+    site taken between cube rows or from the lower sites' neighbouring
+    cubes), against the oracle step by step (complex128) and in the
+    thermodynamics (complex64)."""
+    w = random_system(np.random.default_rng(4100 + top), [1, 2, 1, top])   # d = 2*3*2*(top+1)
+    s = F.System.from_dict(w)
+    R = 8
+    o = oracle.ftlm(osys(w), R=R, M=30, T=T, seed=3)
+    g = F.run(s, R=R, M=30, T=T, seed=3, dtype="c128")
+    assert g["shape"]["site_cube"] == top + 1 and g["shape"]["vector_major"] == 1
+    compare_tridiag(g, o, 1e-10)
+    g64 = F.run(s, R=R, M=30, T=T, seed=3, dtype="c64")
+    assert g64["shape"]["site_cube"] == top + 1
+    compare_tridiag(g64, o, 2e-5, steps=5)
+    for k in KEYS:
+        assert rel(g64[k], o[k], 1e-3, T >= 0.1) < 1e-4, k
+
+
+def test_ftlm_site_cube_batch_matches_single_runs():
+    """A batch whose systems share the top spin (s = 1, sizes 3^5 .. 3^7)
+    takes the cube kernel over the prefix-summed tiles of all instances and
+    gives each system's single-run result (complex128)."""
+    ws = [W.chain(n, Bdir=(1.0, 0.5, 0.3)) for n in (5, 6, 7)]
+    systems = [F.System.from_dict(w) for w in ws]
+    R, M = 8, 20
+    res = F.run_batch(systems, R=R, M=M, T=T, seed=4, dtype="c128")
+    assert all(r["shape"]["site_cube"] == 3 for r in res)
+    for w, r in zip(ws, res):
+        o = oracle.ftlm(osys(w), R=R, M=M, T=T, seed=4)
+        compare_tridiag(r, o, 1e-10)
+    for s_ in systems:
+        s_.close()
+
+
+def test_tune_shape_vector_major_general():
+    """ftlm_tune_shape with cube_bits 0 and multipass 1 forces the
+    vector-major general gather: group_vectors 0 (one row a thread) or a
+    cube group size, tile_cubes x 256 rows or bases per tile; invalid values
+    are rejected.  Every forced shape gives the same scalars (complex128)."""
+    w = random_system(np.random.default_rng(4242), [2, 1, 2, 2])   # d = 54, top site s = 1
+    s = F.System.from_dict(w)
+    R, M = 8, 20
+    with pytest.raises(F.FtlmError):
+        F.tune_shape(s, R, "c128", 0, 3, 1, 1)      # 3 does not divide 8
+    with pytest.raises(F.FtlmError):
+        F.tune_shape(s, R, "c128", 0, 4, 1, 2)      # multipass must be 0 or 1
+    with pytest.raises(F.FtlmError):
+        F.tune_shape(s, R, "c128", 0, 4, 0, 1)      # tile_cubes must be >= 1
+    o = oracle.ftlm(osys(w), R=R, M=M, T=T, seed=6)
+    shapes = {}
+    try:
+        for gv, tc in ((0, 1), (0, 4), (4, 1), (4, 2)):
+            F.tune_shape(s, R, "c128", 0, gv, tc, 1)
+            g = F.run(s, R=R, M=M, T=T, seed=6, dtype="c128")
+            assert g["shape"]["vector_major"] == 1 and g["shape"]["site_cube"] == (3 if gv else 0)
+            assert g["shape"]["tile_rows"] == 256 * tc
+            compare_tridiag(g, o, 1e-10)
+            shapes[(gv, tc)] = g["shape"]
+        F.tune_shape(s, R, "c128", 0, 1, 2, 0)      # the row-major general kernel
+        g = F.run(s, R=R, M=M, T=T, seed=6, dtype="c128")
+        assert g["shape"]["vector_major"] == 0
+        compare_tridiag(g, o, 1e-10)
+    finally:
+        F.tune_shape(s, R, "c128", -1)
+        s.close()

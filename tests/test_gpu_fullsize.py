@@ -129,15 +129,16 @@ def test_ladder_vector_major_run_first_steps():
 
 
 def test_general_block_beyond_l2_first_steps_and_autotune():
-    """An s = 1 chain of 12 sites (d = 531,441) with R = 32 complex128
-    vectors: its block (272 MB) exceeds L2, so a run takes the row-major
-    general gather by default; alpha_0, beta_0, p_0 of every vector equal the
+    """An s = 1 chain of 12 sites (d = 531,441) with R = 30 complex128
+    vectors: its block (255 MB) exceeds L2 and no register-cube group size
+    (4) divides R, so a run takes the row-major general gather by default;
+    alpha_0, beta_0, p_0 of every vector equal the
     quantities formed from the oracle's start vectors with ftlm_apply_h and
     ftlm_apply_sdir.  The autotuner (which also times the vector-major
     general gather) then picks a shape whose run gives the same scalars."""
     w = max(W.WORKLOADS["chains_s1_x24"]["system"](), key=lambda v: int(np.prod(v["two_s"] + 1)))
     s = F.System.from_dict(w)
-    d, R = s.dim, 32
+    d, R = s.dim, 30
     assert d == 3 ** 12
     torch = torch_cuda()
     g = F.run(s, R=R, M=2, T=T, seed=7, dtype="c128")
@@ -163,3 +164,32 @@ def test_general_block_beyond_l2_first_steps_and_autotune():
     finally:
         F.tune_shape(s, R, "c128", -1)
         s.close()
+
+
+def test_site_cube_chain_first_steps():
+    """An s = 1 chain of 11 sites (d = 177,147, a block of 8 complex128
+    vectors fits L2): the run takes the general gather with a register cube
+    of the top site's 3 rows; alpha_0, beta_0, p_0 of every vector equal the
+    quantities formed from the oracle's start vectors with ftlm_apply_h and
+    ftlm_apply_sdir (complex128), and within FP32 rounding in complex64."""
+    w = W.chain(11, Bdir=(1.0, 0.5, 0.3))
+    s = F.System.from_dict(w)
+    d, R = s.dim, 8
+    torch = torch_cuda()
+    x = torch.from_numpy(np.ascontiguousarray(oracle.start_vectors(d, R, seed=9))).cuda()
+    hx = torch.empty_like(x)
+    F.apply_h(s, x, hx, R, "c128")
+    ux = torch.empty_like(x)
+    F.apply_sdir(s, x, ux, R, "c128")
+    a0 = torch.sum(x.conj() * hx, dim=0).real
+    b0 = torch.linalg.vector_norm(hx - a0[None, :] * x, dim=0)
+    p0 = torch.sum(x.conj() * ux, dim=0)
+    a0, b0, p0 = a0.cpu().numpy(), b0.cpu().numpy(), p0.cpu().numpy()
+    scale = np.maximum(np.abs(a0), b0)
+    for dtype, tol in (("c128", 1e-10), ("c64", 1e-5)):
+        g = F.run(s, R=R, M=2, T=T, seed=9, dtype=dtype)
+        assert g["shape"]["site_cube"] == 3, dtype
+        assert np.all(np.abs(g["alpha"][:, 0] - a0) < tol * scale), dtype
+        assert np.all(np.abs(g["beta"][:, 0] - b0) < tol * scale), dtype
+        assert np.all(np.abs(g["p"][:, 0] - p0) < tol * np.maximum(1.0, np.abs(p0))), dtype
+    s.close()
