@@ -70,6 +70,9 @@ def gather_kernel_name(shp):
     """The H.v kernel a launch shape names."""
     if shp.get("vector_major") and shp.get("cube_bits", 0) > 0:
         return f"vm_kernel<float,{shp['cube_bits']}> (vector-major spin-1/2 gather)"
+    if shp.get("vector_major") and shp.get("site_cube", 0) > 0:
+        return (f"cube_gather_kernel<float,{shp['site_cube']},{shp['group_vectors']}> (vector-major general gather, "
+                f"register cube of the top site's {shp['site_cube']} rows)")
     if shp.get("vector_major"):
         return f"rows_vm_kernel<float,{shp['group_vectors']}> (vector-major general gather)"
     if shp.get("cube_bits", 0) > 0:
@@ -653,22 +656,28 @@ def run_profile(args):
 
 
 def run_profile_batch(args):
-    """One run of the uneven batch (24 s = 1 chains x field directions, R = 16,
-    M = 120, complex64, one graph) with the library's default launch shape
-    (which the autotuner also picks for it): device time of the whole graph
-    from CUDA events, for comparison with the summed kernel durations of an
-    ncu launch list of the same command (the difference is the launch gaps)."""
+    """One run of a batch workload (--batch-workload: the 24 s = 1 chains x
+    field directions, R = 16, M = 120, or the 10-direction Mn9-like powder
+    batch, R = 8, M = 40; complex64, one graph) with the library's default
+    launch shape or --shape (cube_bits,group_vectors,tile_cubes,multipass as
+    in ftlm_tune_shape, set for the largest system): device time of the whole
+    graph from CUDA events, for comparison with the summed kernel durations
+    of an ncu launch list of the same command (the difference is the launch
+    gaps)."""
     import torch
 
     import paper_2607_25585_gb300 as F
 
     F.build()
-    spec = W.WORKLOADS["chains_s1_x24"]
+    spec = W.WORKLOADS[args.batch_workload]
     systems = [F.System.from_dict(w) for w in spec["system"]()]
     R, M = spec["R"], spec["M"]
+    if args.shape:
+        F.tune_shape(max(systems, key=lambda s: s.dim), R, "c64", *[int(v) for v in args.shape.split(",")])
     T = W.temperatures()
     stream = torch.cuda.Stream()
-    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream)
+    kw = dict(R=R, M=M, T=T, seed=spec["seed"], dtype="c64", stream=stream,
+              start="pairs" if args.batch_workload == "mn9_powder" else "random")
     F.run_batch(systems, **kw)  # captures the graph
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -676,7 +685,7 @@ def run_profile_batch(args):
     res = F.run_batch(systems, **kw)
     e1.record(stream)
     torch.cuda.synchronize()
-    return {"mode": "profile_batch", "instances": len(systems), "R": R, "M": M,
+    return {"mode": "profile_batch", "workload": args.batch_workload, "instances": len(systems), "R": R, "M": M,
             "graph_ms": e0.elapsed_time(e1), "kernel_launches": res[0]["kernel_launches"],
             "launch_shape": res[0]["shape"]}
 
@@ -737,7 +746,11 @@ def main():
                     help="workload of --hv-only (a batch uses its largest instance)")
     ap.add_argument("--shape", default="", help="cube_bits,group_vectors,tile_cubes[,multipass] for the main run")
     ap.add_argument("--profile-run", default="", help="R,M: one short run of --hv-workload (for profilers)")
-    ap.add_argument("--profile-batch", action="store_true", help="one run of the 24-chain batch (for profilers)")
+    ap.add_argument("--profile-batch", action="store_true", help="one run of a batch workload (for profilers)")
+    ap.add_argument("--batch-workload", default="chains_s1_x24", choices=["chains_s1_x24", "mn9_powder"],
+                    help="the batch --profile-batch runs")
+    ap.add_argument("--profile-sym", action="store_true",
+                    help="the symmetric-estimator leg alone: Mn9-like system, one direction (for profilers)")
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate launch shapes first (default: the library's default plan, which "
                          "keeps the command's kernels the same under a profiler)")
@@ -747,6 +760,14 @@ def main():
         return
     if args.profile_batch:
         print(json.dumps(run_profile_batch(args)))
+        return
+    if args.profile_sym:
+        import torch
+
+        import paper_2607_25585_gb300 as F
+
+        F.build()
+        print(json.dumps(sftlm_leg(F, W.temperatures(), torch.cuda.Stream())))
         return
     if args.hv_only:
         print(json.dumps(run_hv_only(args)), flush=True)

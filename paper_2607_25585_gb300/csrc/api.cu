@@ -417,12 +417,13 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
       }
     pl.gvm_groups = (int)pl.tile_start_g.size() - 1;
     pl.gvm_ntiles = pl.tile_start_g.back();
-    pl.gvm_smem = pl.smem;  // the same tables and per-thread columns as the streaming plan
     int per_sm = 1;
     if (cube) {
+      pl.gvm_smem = gather_smem_bytes(pl.base, c64, 256);  // tables and per-thread columns, no reduction space
       CKI(prepare_cube(Q, V, c64, std::max<size_t>(pl.gvm_smem, 48 * 1024)));
       per_sm = cube_ctas_per_sm(Q, V, c64, 256, pl.gvm_smem);
     } else {
+      pl.gvm_smem = pl.smem;  // the same tables and per-thread columns as the streaming plan
       CKI(prepare_rows_vm(V, c64, std::max<size_t>(pl.gvm_smem, 48 * 1024)));
       per_sm = rows_vm_ctas_per_sm(V, c64, 256, pl.gvm_smem);
     }

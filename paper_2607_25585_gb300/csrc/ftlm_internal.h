@@ -225,6 +225,8 @@ int launch_rows_vm(const LaunchArgs& a, int V, int c64, int grid, int threads, s
 // bases (rows with top digit 0).
 int cube_vectors(int Q, int c64, int want = 0);
 int prepare_cube(int Q, int V, int c64, size_t smem);
+// shared memory of rows_vm_kernel and cube_gather_kernel (no reduction space)
+size_t gather_smem_bytes(const LaunchArgs& a, int c64, int threads);
 int cube_ctas_per_sm(int Q, int V, int c64, int threads, size_t smem);
 int launch_cube(const LaunchArgs& a, int Q, int V, int c64, int grid, int threads, size_t smem, void* stream);
 int device_sm_count();

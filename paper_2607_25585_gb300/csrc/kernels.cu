@@ -560,6 +560,18 @@ size_t rows_smem_bytes(const LaunchArgs& a, int c64, int threads, int Vmax) {
   return off;
 }
 
+// The general gathers that carve no reduction space (rows_vm_kernel,
+// cube_gather_kernel): tables, strides, radices, per-thread m and digit columns.
+size_t gather_smem_bytes(const LaunchArgs& a, int c64, int threads) {
+  const size_t realsz = c64 ? 4 : 8;
+  size_t off = ((size_t)a.tab_reals * realsz + 15) & ~size_t(15);
+  off += (size_t)a.max_n * 8;
+  off += ((size_t)a.max_n * 4 + 15) & ~size_t(15);
+  off += ((size_t)a.max_n * threads * realsz + 15) & ~size_t(15);
+  off += (size_t)a.max_n * threads;
+  return off;
+}
+
 template <typename real, int V, int MODE>
 static int launch_one(const LaunchArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
   rows_kernel<real, V, MODE><<<grid, threads, smem, st>>>(a);

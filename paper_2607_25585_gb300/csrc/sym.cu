@@ -136,10 +136,11 @@ __global__ void __launch_bounds__(kSymThreads, sizeof(real) == 4 ? 2 : 1) sym_om
     }
 }
 
-// W_k = (u.S) q_k for every stored vector k (Vs order), row tiles of one
-// vector in consecutive CTAs (blockIdx.x fastest) so that a vector's
-// single-site neighbourhood is read from HBM once and then served by L2.
-template <typename real>
+// W_k = (u.S) q_k for every stored vector k (Vs order), V consecutive stored
+// vectors a thread (the row's digits and coefficients formed once for them),
+// row tiles of one group in consecutive CTAs (blockIdx.x fastest) so that the
+// group's single-site neighbourhood is read from HBM once and then served by L2.
+template <typename real, int V>
 __global__ void __launch_bounds__(256) sym_sdir_kernel(const InstDesc d, const real* __restrict__ Vs,
                                                      real* __restrict__ Wv, int rows_per_cta) {
   using v2 = typename Cx<real>::v2;
@@ -148,15 +149,17 @@ __global__ void __launch_bounds__(256) sym_sdir_kernel(const InstDesc d, const r
   const int qm = L.qmax, n = d.n;
   const real uz = (real)d.obs[0], aur = (real)d.obs[1], aui = (real)d.obs[2];
   const long long dim = d.dim;
-  const v2* x = reinterpret_cast<const v2*>(Vs) + (size_t)blockIdx.y * (size_t)dim;
-  v2* w = reinterpret_cast<v2*>(Wv) + (size_t)blockIdx.y * (size_t)dim;
+  const v2* x = reinterpret_cast<const v2*>(Vs) + (size_t)blockIdx.y * V * (size_t)dim;
+  v2* w = reinterpret_cast<v2*>(Wv) + (size_t)blockIdx.y * V * (size_t)dim;
   const long long lo = (long long)blockIdx.x * rows_per_cta;
   const long long hi = min(dim, lo + rows_per_cta);
   const bool idx32 = dim <= 0xffffffffll;  // 32-bit digit division when the rows allow it
   for (long long mu = lo + threadIdx.x; mu < hi; mu += blockDim.x) {
     unsigned long long rem = (unsigned long long)mu;
     unsigned rem32 = (unsigned)mu;
-    real ar = 0, ai = 0, ms = 0;
+    real ar[V], ai[V], ms = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) ar[v] = ai[v] = 0;
     for (int k = 0; k < n; ++k) {
       const int qk = __ldg(d.q + k);
       int a;
@@ -173,22 +176,38 @@ __global__ void __launch_bounds__(256) sym_sdir_kernel(const InstDesc d, const r
       const long long st = __ldg(d.stride + k);
       if (a >= 1) {  // a S^+ : from mu - stride
         const real c = t[L.off_up1 + k * qm + a];
-        const v2 xv = __ldg(x + mu - st);
-        ar += c * (aur * xv.x - aui * xv.y);
-        ai += c * (aur * xv.y + aui * xv.x);
+        const real cr = c * aur, ci = c * aui;
+        v2 xv[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) xv[v] = __ldg(x + (size_t)v * dim + mu - st);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          ar[v] += cr * xv[v].x - ci * xv[v].y;
+          ai[v] += cr * xv[v].y + ci * xv[v].x;
+        }
       }
       if (a + 1 < qk) {  // conj(a) S^- : from mu + stride
         const real c = t[L.off_dn1 + k * qm + a];
-        const v2 xv = __ldg(x + mu + st);
-        ar += c * (aur * xv.x + aui * xv.y);
-        ai += c * (aur * xv.y - aui * xv.x);
+        const real cr = c * aur, ci = c * aui;
+        v2 xv[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) xv[v] = __ldg(x + (size_t)v * dim + mu + st);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          ar[v] += cr * xv[v].x + ci * xv[v].y;
+          ai[v] += cr * xv[v].y - ci * xv[v].x;
+        }
       }
     }
-    const v2 xv = __ldg(x + mu);
-    v2 o;
-    o.x = ar + uz * ms * xv.x;
-    o.y = ai + uz * ms * xv.y;
-    w[mu] = o;
+    const real dz = uz * ms;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const v2 xv = __ldg(x + (size_t)v * dim + mu);
+      v2 o;
+      o.x = ar[v] + dz * xv.x;
+      o.y = ai[v] + dz * xv.y;
+      w[(size_t)v * dim + mu] = o;
+    }
   }
 }
 
@@ -234,9 +253,19 @@ int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, in
   cudaError_t e;
   {  // (u.S) q_k of every stored vector, vector by vector
     const int trows = 1024;
-    const dim3 g1((unsigned)((dim + trows - 1) / trows), (unsigned)(R * M));
-    if (c64) sym_sdir_kernel<float><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, trows);
-    else sym_sdir_kernel<double><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, trows);
+    const int nv = R * M, V = nv % 8 == 0 ? 8 : (nv % 4 == 0 ? 4 : (nv % 2 == 0 ? 2 : 1));
+    const dim3 g1((unsigned)((dim + trows - 1) / trows), (unsigned)(nv / V));
+    if (c64) {
+      if (V == 8) sym_sdir_kernel<float, 8><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, trows);
+      else if (V == 4) sym_sdir_kernel<float, 4><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, trows);
+      else if (V == 2) sym_sdir_kernel<float, 2><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, trows);
+      else sym_sdir_kernel<float, 1><<<g1, 256, 0, st>>>(*h, (const float*)Vs, (float*)W, trows);
+    } else {
+      if (V == 8) sym_sdir_kernel<double, 8><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, trows);
+      else if (V == 4) sym_sdir_kernel<double, 4><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, trows);
+      else if (V == 2) sym_sdir_kernel<double, 2><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, trows);
+      else sym_sdir_kernel<double, 1><<<g1, 256, 0, st>>>(*h, (const double*)Vs, (double*)W, trows);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
   }
