@@ -284,11 +284,12 @@ def measured_traffic(shape):
     except Exception:
         return None
     for rec in recs:
-        try:
-            src = open(os.path.join(ROOT, rec["source_file"]), "rb").read()
-        except OSError:
+        try:  # every source file of the kernel as it was when the counters were taken
+            same = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                       for f, h in rec["sources"].items())
+        except (OSError, KeyError):
             continue
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        if not same:
             continue
         if any(rec["shape"][k] != shape.get(k) for k in rec["shape"]):
             continue

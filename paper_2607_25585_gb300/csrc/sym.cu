@@ -9,10 +9,10 @@
 //
 // W_k = (u.S) q_k is formed first for every stored vector, vector after
 // vector so that each vector's single-site neighbourhood stays in L2; then a
-// contraction kernel in which a CTA owns one vector r, a 64 x 64 block of
+// contraction kernel in which a CTA owns one vector r, a 16T x 16T block of
 // (i, j) and a range of rows.  Per tile of 64 rows (32 in complex128) it
 // stages q_i (the i block) and W_j (the j block) in shared memory, and every
-// thread accumulates 4 x 4 entries of G (rows ti + 16a, columns tj + 16b of
+// thread accumulates T x T entries of G (rows ti + 16a, columns tj + 16b of
 // the block) in registers.  The CTA writes its partial block; a second
 // kernel adds the partials of all row ranges in a fixed order in FP64
 // (deterministic for a given launch shape).
@@ -30,7 +30,7 @@ namespace ftlm {
 
 namespace {
 
-constexpr int kSymBlock = 64;  // i and j block
+constexpr int kSymBlock = 64;  // the largest i and j block (T = 4)
 constexpr int kSymThreads = 256;
 
 // rows per shared-memory tile: 64 complex64 or 32 complex128
@@ -39,35 +39,39 @@ struct SymRows {
   static constexpr int value = sizeof(real) == 4 ? 64 : 32;
 };
 
-// Dynamic shared memory: the A and B tiles.
-template <typename real>
+// Dynamic shared memory: the A and B tiles of blocks of 16 T vectors.
+template <typename real, int T>
 struct SymLayout {
   static constexpr int kRows = SymRows<real>::value;
   static constexpr int kPitch = kRows + 1;
-  static size_t tile_bytes() { return sizeof(typename Cx<real>::v2) * kSymBlock * kPitch; }
+  static constexpr int kB = 16 * T;
+  static size_t tile_bytes() { return sizeof(typename Cx<real>::v2) * kB * kPitch; }
 };
 
-// grid: x = row range, y = (i block, j block), z = vector r.  Gp partials
-// [r][range][M][M] complex FP64 (this CTA's block only).
-// The contraction G_r = Q_r^H W_r.  The next tile's loads are issued into registers before the current tile's
+// The contraction G_r = Q_r^H W_r over blocks of kB = 16 T vectors (T x T
+// entries a thread; T = 3 covers M = 40 with 48-blocks instead of padding it
+// to 64).  grid: x = row range, y = (i block, j block), z = vector r.  Gp
+// partials [r][range][M][M] complex FP64 (this CTA's block only).  The next
+// tile's loads are issued into registers before the current tile's
 // multiply-adds (all of a thread's loads in flight at once), so their latency
 // is hidden behind the arithmetic instead of paid once per element.
-template <typename real>
+template <typename real, int T>
 __global__ void __launch_bounds__(kSymThreads, sizeof(real) == 4 ? 2 : 1) sym_omat_kernel(const real* __restrict__ Vs,
                                                                const real* __restrict__ Wv, long long dim, int R,
                                                                int M, long long rows_per_range, int nbj,
                                                                double* __restrict__ Gp) {
   using v2 = typename Cx<real>::v2;
-  using Lay = SymLayout<real>;
-  constexpr int kRows = Lay::kRows, kPitch = Lay::kPitch;
-  constexpr int kPer = kSymBlock * kRows / kSymThreads;  // tile elements per thread
+  using Lay = SymLayout<real, T>;
+  constexpr int kRows = Lay::kRows, kPitch = Lay::kPitch, kB = Lay::kB;
+  constexpr int kPer = kB * kRows / kSymThreads;  // tile elements per thread
+  static_assert(kB * kRows % kSymThreads == 0, "tile elements per thread");
   extern __shared__ __align__(16) unsigned char smem[];
-  v2* A = reinterpret_cast<v2*>(smem);  // [kSymBlock][kPitch]
-  v2* B = A + kSymBlock * kPitch;       // [kSymBlock][kPitch]
+  v2* A = reinterpret_cast<v2*>(smem);  // [kB][kPitch]
+  v2* B = A + kB * kPitch;              // [kB][kPitch]
   const int r = blockIdx.z;
   const int ib = blockIdx.y / nbj, jb = blockIdx.y % nbj;
-  const int i0 = ib * kSymBlock, j0 = jb * kSymBlock;
-  const int ni = min(kSymBlock, M - i0), nj = min(kSymBlock, M - j0);
+  const int i0 = ib * kB, j0 = jb * kB;
+  const int ni = min(kB, M - i0), nj = min(kB, M - j0);
   const long long mu_lo = (long long)blockIdx.x * rows_per_range;
   const long long mu_hi = min(dim, mu_lo + rows_per_range);
   const size_t vstride = (size_t)R * (size_t)dim;
@@ -75,11 +79,11 @@ __global__ void __launch_bounds__(kSymThreads, sizeof(real) == 4 ? 2 : 1) sym_om
   const v2* bbase = reinterpret_cast<const v2*>(Wv) + (size_t)r * (size_t)dim + (size_t)j0 * vstride;
   const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
   const int na = (ni - ti + 15) / 16, nbb = (nj - tj + 15) / 16;
-  real gr[4][4], gi[4][4];
+  real gr[T][T], gi[T][T];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < T; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) gr[a][b] = gi[a][b] = 0;
+    for (int b = 0; b < T; ++b) gr[a][b] = gi[a][b] = 0;
   v2 pa[kPer], pb[kPer];
   auto load = [&](long long m0) {
     const int nt = (int)min((long long)kRows, mu_hi - m0);
@@ -106,16 +110,16 @@ __global__ void __launch_bounds__(kSymThreads, sizeof(real) == 4 ? 2 : 1) sym_om
     __syncthreads();
     if (m0 + kRows < mu_hi) load(m0 + kRows);
     for (int tt = 0; tt < nt; ++tt) {
-      v2 av[4], bv[4];
+      v2 av[T], bv[T];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = A[(ti + 16 * a) * kPitch + tt];
+      for (int a = 0; a < T; ++a) av[a] = A[(ti + 16 * a) * kPitch + tt];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = B[(tj + 16 * b) * kPitch + tt];
+      for (int b = 0; b < T; ++b) bv[b] = B[(tj + 16 * b) * kPitch + tt];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
+      for (int a = 0; a < T; ++a) {
         if (a >= na) break;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < T; ++b) {
           if (b >= nbb) break;
           gr[a][b] = fma(av[a].x, bv[b].x, fma(av[a].y, bv[b].y, gr[a][b]));
           gi[a][b] = fma(av[a].x, bv[b].y, fma(-av[a].y, bv[b].x, gi[a][b]));
@@ -125,9 +129,9 @@ __global__ void __launch_bounds__(kSymThreads, sizeof(real) == 4 ? 2 : 1) sym_om
   }
   double* out = Gp + ((size_t)r * gridDim.x + blockIdx.x) * (size_t)M * M * 2;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < T; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < T; ++b) {
       const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * b;
       if (a < na && b < nbb) {
         out[2 * ((size_t)i * M + j)] = (double)gr[a][b];
@@ -241,15 +245,41 @@ int sym_ranges(long long dim, int R, int M) {
   return (int)std::min<long long>(ranges, 1 << 20);
 }
 
+namespace {
+
+template <typename real, int T>
+cudaError_t launch_omat(const void* Vs, const void* W, long long dim, int R, int M, int nranges, double* Gp,
+                        cudaStream_t st) {
+  constexpr int kB = SymLayout<real, T>::kB;
+  const int nb = (M + kB - 1) / kB;
+  if ((long long)nb * nb > 65535) return cudaErrorInvalidValue;
+  const long long rows = (dim + nranges - 1) / nranges;
+  const dim3 grid((unsigned)nranges, (unsigned)(nb * nb), (unsigned)R);
+  const size_t smem = 2 * SymLayout<real, T>::tile_bytes();
+  cudaError_t e = cudaFuncSetAttribute(sym_omat_kernel<real, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  sym_omat_kernel<real, T><<<grid, kSymThreads, smem, st>>>((const real*)Vs, (const real*)W, dim, R, M, rows, nb, Gp);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_omat_t(const void* Vs, const void* W, long long dim, int R, int M, int nranges, double* Gp,
+                          cudaStream_t st) {
+  const int T = std::min(4, (M + 15) / 16);  // the smallest blocks that cover M (at most 64)
+  if (T == 1) return launch_omat<real, 1>(Vs, W, dim, R, M, nranges, Gp, st);
+  if (T == 2) return launch_omat<real, 2>(Vs, W, dim, R, M, nranges, Gp, st);
+  if (T == 3) return launch_omat<real, 3>(Vs, W, dim, R, M, nranges, Gp, st);
+  return launch_omat<real, 4>(Vs, W, dim, R, M, nranges, Gp, st);
+}
+
+}  // namespace
+
 int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, int nranges, double* Gp, double* G,
                     int c64, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (!W || R < 1 || R > 65535 || M < 1 || nranges < 1 || h->n > kMaxSites) return (int)cudaErrorInvalidValue;
-  const int nb = (M + kSymBlock - 1) / kSymBlock;
-  if ((long long)nb * nb > 65535 || (long long)R * M > 65535) return (int)cudaErrorInvalidValue;
+  if ((long long)R * M > 65535) return (int)cudaErrorInvalidValue;
   const long long dim = h->dim;
-  const long long rows = (dim + nranges - 1) / nranges;
-  const dim3 grid((unsigned)nranges, (unsigned)(nb * nb), (unsigned)R);
   cudaError_t e;
   {  // (u.S) q_k of every stored vector, vector by vector
     const int trows = 1024;
@@ -269,20 +299,8 @@ int launch_sym_omat(const InstDesc* h, const void* Vs, void* W, int R, int M, in
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
   }
-  if (c64) {
-    const size_t smem = 2 * SymLayout<float>::tile_bytes();
-    e = cudaFuncSetAttribute(sym_omat_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    sym_omat_kernel<float><<<grid, kSymThreads, smem, st>>>((const float*)Vs, (const float*)W, dim, R, M, rows, nb,
-                                                              Gp);
-  } else {
-    const size_t smem = 2 * SymLayout<double>::tile_bytes();
-    e = cudaFuncSetAttribute(sym_omat_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    sym_omat_kernel<double><<<grid, kSymThreads, smem, st>>>((const double*)Vs, (const double*)W, dim, R, M, rows,
-                                                               nb, Gp);
-  }
-  e = cudaGetLastError();
+  e = c64 ? launch_omat_t<float>(Vs, W, dim, R, M, nranges, Gp, st)
+          : launch_omat_t<double>(Vs, W, dim, R, M, nranges, Gp, st);
   if (e != cudaSuccess) return (int)e;
   const long long total = (long long)R * M * M;
   sym_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Gp, R, M, nranges, G);

@@ -1,6 +1,6 @@
 """GPU parity of symmetric FTLM (Eqs. E-2-G, E-2-H): the stored Lanczos
 vectors, the matrix O_ij = <v_i|u.S|v_j> formed on the device (u.S on the
-stored vectors, batched complex GEMM) and the host double sum, against the
+stored vectors, then their contraction with the stored vectors) and the host double sum, against the
 FP64 oracle with the same random vectors.  complex128: O over the first 15
 steps to 1e-10 (before the Lanczos runs part by finite precision) and M_B_sym
 to 1e-9 for T >= 0.1 K; complex64: M_B_sym to 1e-4."""
@@ -76,3 +76,28 @@ def test_symmetric_batch_rejected():
     rs = (F.Result * 2)()
     handles = (ctypes.c_void_p * 2)(*[x.handle for x in systems])
     assert F.lib().ftlm_run_batch(2, handles, ctypes.byref(p), rs) != 0
+
+
+@pytest.mark.parametrize("M", [8, 40, 70])
+def test_sftlm_block_sizes(M):
+    """The contraction's blocks of 16, 48 and 64 vectors (T = 1, 3, 4 entries a
+    thread per side; M = 70 spans two blocks per side): O over the first
+    steps against the oracle (complex128, 1e-10), and every entry of O
+    against its Hermitian partner, which the kernel forms from other tiles
+    and, for M = 70, in another CTA."""
+    w = W.square_lattice(4, 3, seed=3)
+    s = F.System.from_dict(w)
+    R = 2
+    o = oracle.sftlm(osys(w), R=R, M=M, T=T, seed=4)
+    g = F.run(s, R=R, M=M, T=T, seed=4, dtype="c128", symmetric=True)
+    for r in range(R):
+        me = int(g["M_eff"][r])
+        assert me == M
+        O = g["O"][r, :me, :me]
+        so = np.abs(O).max()
+        assert np.max(np.abs(O - O.conj().T)) < 1e-12 * so
+        m = min(8, me)
+        assert np.max(np.abs(O[:m, :m] - o["O"][r, :m, :m])) < 1e-10 * so
+        if M > 64:  # entries of the second block row and column
+            assert np.abs(O[64:, :]).max() > 1e-3 * so and np.abs(O[:, 64:]).max() > 1e-3 * so
+    s.close()
