@@ -418,71 +418,50 @@ __device__ __forceinline__ typename Cx<real>::v2 ldx(const void* x, long long id
   return __ldg(reinterpret_cast<const typename Cx<real>::v2*>(x) + idx);
 }
 
-// Last CTA of a launch: the totals of the CTAs' partials and the scalars they
-// set (alpha, p, beta, sigma, breakdown).
+// Last CTA: total[inst][r][c] = sum over the CTAs' partials in a fixed order
+// (four interleaved partial sums, combined in a fixed order), one thread per
+// (inst, r, c): deterministic for a given grid.
+__device__ inline double total_partial(const LaunchArgs& a, int inst, int r, int c) {
+  const double* base = a.partials + (size_t)inst * gridDim.x * (size_t)a.R * kNumPartials + (size_t)r * kNumPartials + c;
+  const size_t stride = (size_t)a.R * kNumPartials;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int b = 0;
+  for (; b + 4 <= (int)gridDim.x; b += 4) {
+    s0 += base[(size_t)b * stride];
+    s1 += base[(size_t)(b + 1) * stride];
+    s2 += base[(size_t)(b + 2) * stride];
+    s3 += base[(size_t)(b + 3) * stride];
+  }
+  for (; b < (int)gridDim.x; ++b) s0 += base[(size_t)b * stride];
+  return (s0 + s1) + (s2 + s3);
+}
+
 __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
   // (inst_all points at the device array, or at the inline descriptor)
-  // Each (instance, vector) item's partials over the CTAs are summed by a
-  // group of L lanes of one warp (L the largest power of two <= 32 with
-  // items x L <= blockDim): lane k of the group adds CTAs k, k + L, ... and
-  // the group's lanes are combined by a fixed xor tree, so the result is
-  // deterministic for a given grid and block.
   const int R = a.R;
-  const int nitems = a.n_inst * R;
-  int L = 32;
-  while (L > 1 && nitems * L > (int)blockDim.x) L >>= 1;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane & (L - 1);                      // lane within the group
-  const int ngroups = (int)(blockDim.x / 32) * (32 / L);
-  const int group = (int)(threadIdx.x / 32) * (32 / L) + lane / L;
-  const int rounds = (nitems + ngroups - 1) / ngroups;  // the same for every thread: shuffles stay converged
-  const size_t stride = (size_t)R * kNumPartials;
-  for (int round = 0; round < rounds; ++round) {
-    const int item = round * ngroups + group;
-    double t[3] = {0.0, 0.0, 0.0};
-    if (item < nitems) {
-      const int inst = item / R, r = item % R;
-      const double* base = a.partials + (size_t)inst * gridDim.x * stride + (size_t)r * kNumPartials;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int b = sub;
-        for (; b + 3 * L < (int)gridDim.x; b += 4 * L) {
-          s0 += base[(size_t)b * stride + c];
-          s1 += base[(size_t)(b + L) * stride + c];
-          s2 += base[(size_t)(b + 2 * L) * stride + c];
-          s3 += base[(size_t)(b + 3 * L) * stride + c];
-        }
-        for (; b < (int)gridDim.x; b += L) s0 += base[(size_t)b * stride + c];
-        t[c] = (s0 + s1) + (s2 + s3);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      for (int o = 1; o < L; o <<= 1) t[c] += __shfl_xor_sync(0xffffffffu, t[c], o);
-    if (item >= nitems || sub != 0) continue;
+  for (int item = threadIdx.x; item < a.n_inst * R; item += blockDim.x) {
     const int inst = item / R, r = item % R;
     const InstDesc& d = inst_all[inst];
     const DevScalars& sc = d.sc;
     const int j = a.step;
     if (a.mode == kModeLanczos || a.mode == kModeEpilogue) {
-      sc.alpha[(size_t)j * sc.ss + r] = t[0];
-      sc.p[((size_t)j * sc.ss + r) * 2] = t[1];
-      sc.p[((size_t)j * sc.ss + r) * 2 + 1] = t[2];
+      sc.alpha[(size_t)j * sc.ss + r] = total_partial(a, inst, r, 0);
+      sc.p[((size_t)j * sc.ss + r) * 2] = total_partial(a, inst, r, 1);
+      sc.p[((size_t)j * sc.ss + r) * 2 + 1] = total_partial(a, inst, r, 2);
     } else if (a.mode == kModeApply && a.fused_step) {  // alpha_j = Re<v_j|w'>, p_j = <v_j|u>
       const double sg = sc.sigma[(size_t)j * sc.ss + r];
-      sc.alpha[(size_t)j * sc.ss + r] = sg * t[0];
-      sc.p[((size_t)j * sc.ss + r) * 2] = sg * t[1];
-      sc.p[((size_t)j * sc.ss + r) * 2 + 1] = sg * t[2];
+      sc.alpha[(size_t)j * sc.ss + r] = sg * total_partial(a, inst, r, 0);
+      sc.p[((size_t)j * sc.ss + r) * 2] = sg * total_partial(a, inst, r, 1);
+      sc.p[((size_t)j * sc.ss + r) * 2 + 1] = sg * total_partial(a, inst, r, 2);
     } else if (a.mode == kModeApply) {  // gather_alpha
       const double sg = sc.sigma[(size_t)j * sc.ss + r];
-      sc.alpha[(size_t)j * sc.ss + r] = sg * sg * t[0];
+      sc.alpha[(size_t)j * sc.ss + r] = sg * sg * total_partial(a, inst, r, 0);
     } else if (a.mode == kModeUpdate || a.mode == kModeStep) {
       if (a.mode == kModeStep) {
-        sc.p[((size_t)j * sc.ss + r) * 2] = t[1];
-        sc.p[((size_t)j * sc.ss + r) * 2 + 1] = t[2];
+        sc.p[((size_t)j * sc.ss + r) * 2] = total_partial(a, inst, r, 1);
+        sc.p[((size_t)j * sc.ss + r) * 2 + 1] = total_partial(a, inst, r, 2);
       }
-      const double nrm2 = t[0];
+      const double nrm2 = total_partial(a, inst, r, 0);
       const double bnew = sqrt(fmax(nrm2, 0.0));
       const double al = sc.alpha[(size_t)j * sc.ss + r];
       const double bold = j > 0 ? sc.beta[(size_t)(j - 1) * sc.ss + r] : 0.0;
@@ -500,7 +479,7 @@ __device__ inline void finalize(const LaunchArgs& a, const InstDesc* inst_all) {
       }
       sc.sigma[(size_t)(j + 1) * sc.ss + r] = sig;
     } else if (a.mode == kModeStartNorm) {
-      const double nrm = sqrt(fmax(t[0], 0.0));
+      const double nrm = sqrt(fmax(total_partial(a, inst, r, 0), 0.0));
       sc.sigma[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
       sc.scale[r] = 0.0;
       sc.active[r] = nrm > 0.0 ? 1 : 0;
