@@ -816,6 +816,69 @@ int launch_vm_unit_tables(const double* tab_d, const TabLayout& L, int n, int K,
   return (int)cudaGetLastError();
 }
 
+// y = c (u.S) x on the vector-major block of a spin-1/2 system (R one-vector
+// instances, tiles as in vm_stream_kernel), c = sigma_0 with a.use_sigma0
+// (the start block's observable vector) or 1.  With every s_i = 1/2 a row's
+// digits are its bits: (u.S x)[mu] = u_z (sum_i m_i) x[mu] + sum_i
+// (bit i ? a <1|s+|0> x[mu - 2^i] : conj(a) <0|s-|1> x[mu + 2^i]),
+// a = (u_x - i u_y)/2, the terms and coefficients of the general row form.
+template <typename real>
+__global__ void __launch_bounds__(256) vm_sdir_kernel(const __grid_constant__ LaunchArgs a) {
+  using v2 = typename Cx<real>::v2;
+  __shared__ InstDesc d;
+  __shared__ __align__(16) real site[kMaxSites][4];  // m(down), m(up), <1|s+|0>, <0|s-|1>
+  const int bd = blockDim.x;
+  int cur = -1;
+  real c = 1;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int inst = tile / a.tiles_per_vg;
+    if (inst != cur) {
+      __syncthreads();
+      if (threadIdx.x == 0) d = a.inst[inst];
+      __syncthreads();
+      if (cur < 0) {  // the system's tables (every instance is a vector of the same system)
+        const real* t = reinterpret_cast<const real*>(d.tab);
+        for (int i = threadIdx.x; i < d.n; i += bd) {
+          site[i][0] = t[d.lay.off_m + i * d.lay.qmax];
+          site[i][1] = t[d.lay.off_m + i * d.lay.qmax + 1];
+          site[i][2] = t[d.lay.off_up1 + i * d.lay.qmax + 1];
+          site[i][3] = t[d.lay.off_dn1 + i * d.lay.qmax];
+        }
+        __syncthreads();
+      }
+      c = a.use_sigma0 ? (real)d.sc.sigma[0] : (real)1;
+      cur = inst;
+    }
+    const int n = d.n;
+    const real uz = (real)d.obs[0], aur = (real)d.obs[1], aui = (real)d.obs[2];
+    const v2* x = reinterpret_cast<const v2*>(d.x);
+    v2* y = reinterpret_cast<v2*>(d.y);
+    const long long e0 = (long long)(tile - inst * a.tiles_per_vg) * a.rows_per_tile;
+    const long long e1 = min(e0 + (long long)a.rows_per_tile, d.dim);
+    for (long long mu = e0 + threadIdx.x; mu < e1; mu += bd) {
+      real ar = 0, ai = 0, msum = 0;
+#pragma unroll 4
+      for (int i = 0; i < n; ++i) {  // (unrolled: several sites' gathered loads in flight)
+        const typename Cx<real>::v2 mm = *reinterpret_cast<const v2*>(&site[i][0]);
+        const typename Cx<real>::v2 cc = *reinterpret_cast<const v2*>(&site[i][2]);
+        const bool up = (mu >> i) & 1;
+        msum += up ? mm.y : mm.x;
+        const v2 xv = __ldg(x + (up ? mu - (1ll << i) : mu + (1ll << i)));
+        const real e = up ? cc.x : cc.y;
+        const real cr = aur * e, ci = up ? aui * e : -aui * e;
+        ar = fma(cr, xv.x, fma(-ci, xv.y, ar));
+        ai = fma(cr, xv.y, fma(ci, xv.x, ai));
+      }
+      const v2 xo = __ldg(x + mu);
+      const real dz = uz * msum;
+      v2 o;
+      o.x = c * fma(dz, xo.x, ar);
+      o.y = c * fma(dz, xo.y, ai);
+      y[mu] = o;
+    }
+  }
+}
+
 int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (a.inline_one || (a.rows_per_tile & 1)) return (int)cudaErrorInvalidValue;
@@ -828,6 +891,10 @@ int launch_vm_stream(const LaunchArgs& a, int c64, int grid, void* stream) {
   } else if (a.mode == kModeStartNorm) {
     if (c64) vm_stream_kernel<float, kModeStartNorm><<<grid, 256, 0, st>>>(a);
     else vm_stream_kernel<double, kModeStartNorm><<<grid, 256, 0, st>>>(a);
+  } else if (a.mode == kModeApplyS) {
+    if (a.max_n > kMaxSites) return (int)cudaErrorInvalidValue;
+    if (c64) vm_sdir_kernel<float><<<grid, 256, 0, st>>>(a);
+    else vm_sdir_kernel<double><<<grid, 256, 0, st>>>(a);
   } else {
     return (int)cudaErrorInvalidValue;
   }
