@@ -253,11 +253,13 @@ typedef struct {
   /* launch shape of the H.v launches (see ftlm_tune_shape) */
   int cube_bits;          /* 0: general row kernel; 2..4: spin-1/2 register cubes */
   int passes;             /* launches per H.v (spin-1/2 multi-pass form: ceil(n / cube_bits)) */
-  int group_vectors;      /* register-cube kernel: vectors per group */
+  int group_vectors;      /* vectors processed together (register-cube kernels, general vector-major gathers) */
   int tile_rows;          /* rows per tile */
   int grid;               /* CTAs per H.v launch */
   int threads;            /* threads per CTA */
-  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (multipass 3..9) */
+  int vector_major;       /* 1: the run kept each Lanczos vector contiguous (spin-1/2 multipass
+                             3..9; other spins with cube_bits 0, multipass 1, or the default plan
+                             where the top site's register cube applies or the block fits L2) */
   /* symmetric runs (params.symmetric = 1); caller-allocated, may be NULL */
   double* M_B_sym;        /* [nT] sFTLM: -g sum_r <r|e^{-bH/2} u.S e^{-bH/2}|r> / sum_r <r|e^{-bH}|r>,
                              Eq. (E-2-G) with (E-2-H), shifted by E0 */
