@@ -819,6 +819,20 @@ ftlm_status enqueue_run(RunCtx& ctx, const std::vector<ftlm_system*>& sys, const
       if (tk) CK(cudaEventRecordWithFlags(ctx.ev[4 + 4 * j], st, cudaEventRecordExternal));
       continue;
     }
+    if (pl.gen_vm && pl.gvm_cube) {  // the cube gather writes w' over q_{j-1} and sets alpha_j, p_j
+      LaunchArgs g = a;  // x = q_j, y = q_{j-1}, u
+      g.mode = kModeApply;
+      g.fused_step = 1;
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      CKI(launch_plan(pl, g, st));
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[evi++], st, cudaEventRecordExternal));
+      a.mode = kModeUpdate;
+      CKI(launch_plan(pl, a, st));
+      ctx.launches += 2;
+      ctx.hv_launches++;
+      if (tk) CK(cudaEventRecordWithFlags(ctx.ev[4 + 4 * j], st, cudaEventRecordExternal));
+      continue;
+    }
     if (split) {
       LaunchArgs g = a;
       g.inst = (j % 2 == 0) ? d_gather_even : d_gather_odd;
@@ -1043,7 +1057,7 @@ ftlm_status run_impl(std::vector<ftlm_system*> sys, const ftlm_run_params* p, ft
   if (pl.half.on && !vm_fused_step(pl)) {  // (the fused vector-major step keeps no H q block)
     ftlm_status hs_ = ensure_hq(sys[0], R, c64, (pl.half.vm && !pl.half.hybrid) ? pl.half.passes : 1);
     if (hs_ != FTLM_OK) return hs_;
-  } else if (pl.wideV || pl.gen_vm) {
+  } else if (pl.wideV || (pl.gen_vm && !pl.gvm_cube)) {  // (the cube gather keeps no H q block)
     for (auto* s : sys) {
       ftlm_status hs_ = ensure_hq(s, R, c64, 1);
       if (hs_ != FTLM_OK) return hs_;

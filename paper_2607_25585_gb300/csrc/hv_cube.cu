@@ -59,14 +59,52 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? (Q * V <= 12 ? 3 : 2)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SmemView s = carve<real>(smem_raw, a, 0);
   __shared__ InstDesc d;
+  // Lanczos step (a.fused_step): each thread's sums of Re<q_j|w'>, Re<q_j|u>,
+  // Im<q_j|u> for the group's V vectors ([V * 3][256], a thread's own column),
+  // the group's sigma_j and beta_j sigma_{j-1}, and the last CTA's flag
+  __shared__ real sacc[V * 3 * 256];
+  __shared__ double s_sg[V], s_bsp[V];
+  __shared__ int is_last;
+  const bool fused = a.fused_step != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const InstDesc* insts = a.inline_one ? &a.one : a.inst;
+  const int nvec = a.n_inst * V;  // one-vector instances: the partial sums' slots [vector][CTA][kNumPartials]
+  if (fused) {
+    for (int k = threadIdx.x; k < nvec * kNumPartials; k += blockDim.x)
+      a.partials[((size_t)(k / kNumPartials) * gridDim.x + blockIdx.x) * kNumPartials + k % kNumPartials] = 0.0;
+    for (int k = threadIdx.x; k < V * 3 * 256; k += blockDim.x) sacc[k] = 0;
+  }
+  // the CTA's sums of group g's vectors into its partial slots: warp w adds
+  // items w, w + 8, ... (item = vector x 3 + sum), lanes in a fixed order
+  auto flush = [&](int g) {
+    __syncthreads();
+    for (int item = warp; item < V * 3; item += (int)(blockDim.x >> 5)) {
+      double t = 0.0;
+      for (int k = lane; k < (int)blockDim.x; k += 32) {
+        t += (double)sacc[item * 256 + k];
+        sacc[item * 256 + k] = 0;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0)
+        a.partials[((size_t)(g * V + item / 3) * gridDim.x + blockIdx.x) * kNumPartials + item % 3] = t;
+    }
+    __syncthreads();
+  };
   int cur = -1;
   const void* staged = nullptr;  // tables of the system now in shared memory
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int g = a.inline_one ? 0 : find_instance(a.tile_start, a.n_inst, tile);
     if (g != cur) {
+      if (fused && cur >= 0) flush(cur);
       __syncthreads();
       if (threadIdx.x == 0) d = insts[(size_t)g * V];
+      if (fused && threadIdx.x < V) {  // the group's vectors' step scalars
+        const DevScalars& sc = insts[(size_t)g * V + threadIdx.x].sc;
+        const int j = a.step;
+        s_sg[threadIdx.x] = sc.sigma[(size_t)j * sc.ss];
+        s_bsp[threadIdx.x] = a.first ? 0.0 : sc.beta[(size_t)(j - 1) * sc.ss] * sc.sigma[(size_t)(j - 1) * sc.ss];
+      }
       __syncthreads();
       if (d.tab != staged) {  // the groups of one system share its tables
         stage_instance<real>(d, s);
@@ -274,17 +312,63 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? (Q * V <= 12 ? 3 : 2)
           }
         }
       }
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
+      if (fused) {  // w' = sigma_j H q_j - beta_j sigma_{j-1} q_{j-1} over q_{j-1}; <q_j|w'>, <q_j|u>
+        const v2* u = reinterpret_cast<const v2*>(d.u);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          v2 o;
-          o.x = ar[q][v];
-          o.y = ai[q][v];
-          y[(long long)v * dim + b + (long long)q * sT] = o;
+          const real sg = (real)s_sg[v], bsp = (real)s_bsp[v];
+          real pw = 0, pr = 0, pi = 0;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const long long e = (long long)v * dim + b + (long long)q * sT;
+            v2 w;
+            if (a.first) {
+              w.x = sg * ar[q][v];
+              w.y = sg * ai[q][v];
+            } else {
+              const v2 qp = __ldcs(y + e);
+              w.x = sg * ar[q][v] - bsp * qp.x;
+              w.y = sg * ai[q][v] - bsp * qp.y;
+            }
+            __stcs(y + e, w);
+            const v2 xv = __ldg(x + e);  // own rows of q_j, re-read
+            const v2 uv = __ldcs(u + e);
+            pw += xv.x * w.x + xv.y * w.y;
+            pr += xv.x * uv.x + xv.y * uv.y;
+            pi += xv.x * uv.y - xv.y * uv.x;
+          }
+          sacc[(v * 3 + 0) * 256 + threadIdx.x] += pw;
+          sacc[(v * 3 + 1) * 256 + threadIdx.x] += pr;
+          sacc[(v * 3 + 2) * 256 + threadIdx.x] += pi;
         }
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            v2 o;
+            o.x = ar[q][v];
+            o.y = ai[q][v];
+            y[(long long)v * dim + b + (long long)q * sT] = o;
+          }
+      }
     }
   }
+  if (!fused) return;
+  // the last CTA to arrive sets alpha_j and p_j of every vector
+  if (cur >= 0) flush(cur);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  LaunchArgs f = a;  // the vectors as one-vector instances
+  f.n_inst = nvec;
+  f.R = 1;
+  f.mode = kModeApply;
+  finalize(f, insts);
+  if (threadIdx.x == 0) *a.counter = 0u;
 }
 
 template <typename real, int Q, int V>
