@@ -72,7 +72,7 @@ def gather_kernel_name(shp):
         return f"vm_kernel<float,{shp['cube_bits']}> (vector-major spin-1/2 gather)"
     if shp.get("vector_major") and shp.get("site_cube", 0) > 0:
         return (f"cube_gather_kernel<float,{shp['site_cube']},{shp['group_vectors']}> (vector-major general gather, "
-                f"register cube of the top site's {shp['site_cube']} rows)")
+                f"register cube of the top site's {shp['site_cube']} rows, the step's w' in its epilogue)")
     if shp.get("vector_major"):
         return f"rows_vm_kernel<float,{shp['group_vectors']}> (vector-major general gather)"
     if shp.get("cube_bits", 0) > 0:
@@ -80,10 +80,11 @@ def gather_kernel_name(shp):
     return "rows_kernel (row-major general gather)"
 
 
-def batch_roofline(systems_two_s, dims, R, hv_ms, sm_max_mhz, kernel):
-    """FP32 roofline of one H.v launch over a batch (the general gathers carry
-    no Lanczos epilogue: the step runs in the next launch)."""
-    flops = sum(algorithmic_flops_per_sv(t, epilogue=False) * d * R for t, d in zip(systems_two_s, dims))
+def batch_roofline(systems_two_s, dims, R, hv_ms, sm_max_mhz, kernel, epilogue):
+    """FP32 roofline of one H.v launch over a batch (epilogue: the launch also
+    forms the Lanczos step's w' and its alpha and p sums, as the register-cube
+    gather does; the one-row gathers leave them to the next launch)."""
+    flops = sum(algorithmic_flops_per_sv(t, epilogue=epilogue) * d * R for t, d in zip(systems_two_s, dims))
     achieved = flops / (hv_ms / 1e3) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -413,7 +414,8 @@ def extra_workloads(F, T, stream, args):
                             "roofline": batch_roofline([w["two_s"] for w in ws_], [s.dim for s in systems], R,
                                                        res[0]["hv_ms"] / max(1, res[0]["hv_launches"]),
                                                        load_peaks().get("sm_max_mhz", 2070.0),
-                                                       gather_kernel_name(res[0]["shape"])),
+                                                       gather_kernel_name(res[0]["shape"]),
+                                                       res[0]["shape"].get("site_cube", 0) > 0),
                             "note": "one graph for all 24 instances; shape chosen by the autotuner"}
     for s in systems:
         s.close()
@@ -534,13 +536,14 @@ def mn9_leg(F, T, stream, args):
     mb = np.mean([r["M_B"] for r in res], axis=0)
     hv = res[0]["hv_ms"] / max(1, res[0]["hv_launches"])
     roof = batch_roofline([w["two_s"] for w in ws_], [s.dim for s in systems], R, hv,
-                          load_peaks().get("sm_max_mhz", 2070.0), gather_kernel_name(res[0]["shape"]))
+                          load_peaks().get("sm_max_mhz", 2070.0), gather_kernel_name(res[0]["shape"]),
+                          res[0]["shape"].get("site_cube", 0) > 0)
     for s in systems:
         s.close()
     return {"value": sv / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "M": M, "R": R, "directions": len(systems),
             "d": d, "hv_ms_per_launch": hv, "roofline": roof,
             "launch_shape": res[0]["shape"], "powder_M_B_at_T": {f"{T[i]:.3g}": float(mb[i]) for i in (0, 20, 39)},
-            "note": "one graph for the 10 directions; general mixed-radix kernel"}
+            "note": "one graph for the 10 directions; general mixed-radix gather (launch_shape, roofline.kernel)"}
 
 
 def time_reversal_leg(F, T, stream):
