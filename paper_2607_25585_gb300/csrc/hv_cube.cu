@@ -21,6 +21,12 @@
 // Terms follow the same coefficient conventions as the general row
 // enumeration (rows_common.cuh); they are added in a different order, so
 // results agree with it to rounding.
+//
+// Lanczos steps (a.fused_step): x = q_j, y = q_{j-1}, u; the epilogue writes
+// w' = sigma_j H q_j - beta_j sigma_{j-1} q_{j-1} over q_{j-1} and sums
+// Re<q_j|w'>, <q_j|u> per vector, so the step's update pass follows directly
+// (no H q block and no separate epilogue pass); the last CTA sets alpha_j and
+// p_j.
 #include <cuda_runtime.h>
 
 #include <cstdint>
