@@ -426,7 +426,8 @@ int cube_ctas_per_sm(int Q, int V, int c64, int threads, size_t smem) {
 
 int launch_cube(const LaunchArgs& a, int Q, int V, int c64, int grid, int threads, size_t smem, void* stream) {
   const void* k = cube_pick(Q, V, c64);
-  if (!k || a.mode != kModeApply) return (int)cudaErrorInvalidValue;
+  // (the step's per-thread sums are laid out for 256-thread CTAs)
+  if (!k || a.mode != kModeApply || threads != 256) return (int)cudaErrorInvalidValue;
   void* args[] = {const_cast<LaunchArgs*>(&a)};
   return (int)cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, reinterpret_cast<cudaStream_t>(stream));
 }
