@@ -379,9 +379,18 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
   int Qtop = sys[0]->hs.n >= 2 ? sys[0]->hs.q.back() : 0;
   for (auto* s : sys)
     if (s->hs.n < 2 || s->hs.q.back() != Qtop) Qtop = 0;
-  const int Vdef = Qtop ? cube_vectors(Qtop, c64) : 0;
+  // the cube's group size: the default for the top spin, else 4, whichever
+  // has a kernel and divides R (0: none)
+  auto cube_group = [&](int want) {
+    if (!Qtop) return 0;
+    if (want > 0) return (cube_vectors(Qtop, c64, want) && R % want == 0) ? want : 0;
+    for (int v : {cube_vectors(Qtop, c64), 4})
+      if (v > 0 && cube_vectors(Qtop, c64, v) && R % v == 0) return v;
+    return 0;
+  };
+  const int Vdef = cube_group(0);
   const bool gvm_fits = (long long)big->hs.dim * R * (c64 ? 8 : 16) <= device_l2_bytes();
-  const bool gvm_default = gvm_fits || (Vdef > 0 && R % Vdef == 0);
+  const bool gvm_default = gvm_fits || Vdef > 0;
   const bool want_gvm = pl.sh.general_vm == 1 || (pl.sh.general_vm < 0 && !force && gvm_default);
   if (allow_vm && want_gvm && pl.sh.half_K == 0 && !pl.sh.explicit_general) {
     int V = 1;
@@ -393,8 +402,8 @@ ftlm_status make_plan(const std::vector<ftlm_system*>& sys, int R, int c64, Plan
     // the register cube along the top site when every system has the same top
     // spin and a kernel exists for it and for a group size dividing R
     const int Q = Qtop;
-    const int Vc = (Q && pl.sh.gvm_cube != 0) ? cube_vectors(Q, c64, std::max(0, pl.sh.gvm_cube)) : 0;
-    const bool cube = Vc > 0 && R % Vc == 0;
+    const int Vc = (Q && pl.sh.gvm_cube != 0) ? cube_group(std::max(0, pl.sh.gvm_cube)) : 0;
+    const bool cube = Vc > 0;
     if (cube) V = Vc;
     std::vector<ftlm_system*> vecs;  // one instance per (system, vector), system-major
     for (auto* s : sys)

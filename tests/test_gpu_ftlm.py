@@ -273,8 +273,8 @@ def test_ftlm_general_vector_major_matches_oracle(R):
     # the top site is s = 1/2: a register cube of its 2 rows where the group size divides R
     assert g["shape"]["site_cube"] == (2 if R % 4 == 0 else 0)
     g64 = F.run(s, R=R, M=30, T=T, seed=8, vec_offset=1, dtype="c64")
-    if R % 8 == 0:  # the cube over groups of 8 vectors (complex64, 2s+1 <= 3)
-        assert g64["shape"]["site_cube"] == 2 and g64["shape"]["group_vectors"] == 8
+    if R % 4 == 0:  # the cube over groups of 8 vectors (complex64, 2s+1 <= 3), else of 4
+        assert g64["shape"]["site_cube"] == 2 and g64["shape"]["group_vectors"] == (8 if R % 8 == 0 else 4)
     else:
         assert g64["shape"]["site_cube"] == 0 and g64["shape"]["group_vectors"] == R
     for k in KEYS:
