@@ -452,7 +452,13 @@ def sums_sym(alpha, beta, O, M_eff, g, T):
 
 def tune_shape(sys: System, nvec: int, dtype="c64", cube_bits: int = 0, group_vectors: int = 1,
                tile_cubes: int = 2, multipass: int = 0):
-    """Override the launch shape for (system shape, nvec, dtype) (``ftlm_tune_shape``)."""
+    """Override the launch shape for (system shape, nvec, dtype) (``ftlm_tune_shape``).
+
+    cube_bits = -1 drops the override; cube_bits = 0 selects the general
+    kernel: on the row-major block (multipass 0) or, in runs, on the
+    vector-major block (multipass 1: group_vectors = the register cube's
+    group size, 4 or 8, or 0 for one row a thread; tile_cubes x 256 rows or
+    bases per tile); cube_bits 2..4 select the spin-1/2 register-cube shapes."""
     _check(lib().ftlm_tune_shape(sys.handle, int(nvec), _DTYPES[dtype], int(cube_bits), int(group_vectors),
                                  int(tile_cubes), int(multipass)))
 
