@@ -349,3 +349,18 @@ def test_tune_shape_vector_major_general():
     finally:
         F.tune_shape(s, R, "c128", -1)
         s.close()
+
+
+def test_batch_of_mixed_top_spins_uses_one_row_gather():
+    """A batch whose systems end in different spins has no common register
+    cube: the vector-major gather with one row a thread runs it (the blocks
+    fit L2), and every system's scalars match its oracle run (complex128)."""
+    ws = [random_system(np.random.default_rng(700 + k), ts) for k, ts in enumerate([[1, 2, 1], [2, 1, 2], [3, 2]])]
+    systems = [F.System.from_dict(w) for w in ws]
+    R, M = 8, 20
+    res = F.run_batch(systems, R=R, M=M, T=T, seed=2, dtype="c128")
+    for w, r in zip(ws, res):
+        assert r["shape"]["vector_major"] == 1 and r["shape"]["site_cube"] == 0
+        compare_tridiag(r, oracle.ftlm(osys(w), R=R, M=M, T=T, seed=2), 1e-10)
+    for s_ in systems:
+        s_.close()
