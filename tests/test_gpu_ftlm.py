@@ -355,7 +355,8 @@ def test_batch_of_mixed_top_spins_uses_one_row_gather():
     """A batch whose systems end in different spins has no common register
     cube: the vector-major gather with one row a thread runs it (the blocks
     fit L2), and every system's scalars match its oracle run (complex128)."""
-    ws = [random_system(np.random.default_rng(700 + k), ts) for k, ts in enumerate([[1, 2, 1], [2, 1, 2], [3, 2]])]
+    # d = 36, 36, 48 > M: no system exhausts its Krylov space within the M steps compared
+    ws = [random_system(np.random.default_rng(700 + k), ts) for k, ts in enumerate([[1, 2, 1, 2], [2, 1, 2, 1], [3, 2, 1, 1]])]
     systems = [F.System.from_dict(w) for w in ws]
     R, M = 8, 20
     res = F.run_batch(systems, R=R, M=M, T=T, seed=2, dtype="c128")
