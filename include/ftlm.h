@@ -282,7 +282,11 @@ typedef struct {
  *   Z' = (d/R) sum_r sum_n |U_0n|^2 e^{-beta (eps_n - E0)},  ln Z = ln Z' - beta E0,
  *   E, C from the same weights, M_B = -g Re[sum e^{-beta(eps-E0)} U_0n sum_j U_jn conj(p_j)] / Z'.
  * All R vectors run as one device block; the M steps are captured in one
- * CUDA graph.  Blocks until the results are on the host.
+ * CUDA graph.  The block is vector-major (each vector contiguous) for
+ * spin-1/2 systems and, for other spins, where the general gather can hold
+ * the top site's 2s+1 rows as a register cube or the block fits L2; the
+ * launch shape is reported in the result (cube_bits, site_cube,
+ * vector_major, ...).  Blocks until the results are on the host.
  */
 ftlm_status ftlm_run(const ftlm_system* sys, const ftlm_run_params* p, ftlm_result* res);
 
